@@ -1,0 +1,181 @@
+/*
+ * edm.h -- C ABI of libedm: all-to-all convergent cross mapping (CCM) on one
+ * NVIDIA GB300 (sm_103a), after kEDM (Takahashi, Widanage, Pao; PEARC'21).
+ *
+ * Method (kEDM section 2.1, steps 1-4):
+ *   1. embed a library series X with lag tau in E dimensions:
+ *        x(t) = (X(t), X(t-tau), ..., X(t-(E-1)tau));
+ *   2. find the k = E+1 nearest neighbours t_1..t_k of every library point
+ *      (Euclidean distance, the point itself excluded);
+ *   3. predict a target Y as  Yhat(t+Tp) = sum_r w_r Y(t_r+Tp) / sum_r w_r,
+ *      w_r = exp(-d(t,t_r) / d(t,t_1));
+ *   4. score the prediction with Pearson's rho against Y(t+Tp).
+ * The neighbour table of a library is built once and reused for every target
+ * (closing paragraph of section 2.1).
+ *
+ * Conventions shared by every call:
+ *   - Series are float32, row-major [N][L]; a series is a row.
+ *   - The points of a library are the times P = {t : (E-1)tau <= t <= L-1-Tp};
+ *     n = L-(E-1)tau-Tp of them.  The library set is the prediction set
+ *     (leave-one-out).  Row i of any per-point output is time t = (E-1)tau+i.
+ *   - Neighbours are ranked by the squared distance accumulated in lag order
+ *     with fused multiply-adds; exact ties go to the lower time index.  The
+ *     neighbour sets equal those of an FP64 evaluation of that definition.
+ *   - If the nearest distance is 0 then w_r = 1 for d_r = 0, else 0.
+ *   - A zero-variance prediction or observation gives rho = NaN.
+ *
+ * Memory and streams: every array argument is a DEVICE pointer owned by the
+ * caller (unless stated otherwise); libedm never frees it.  A context owns
+ * its own workspace (neighbour tables, transposed targets), grown on demand
+ * with cudaMalloc and freed by edm_destroy.  All work is enqueued on the
+ * context's stream and is asynchronous to the host.
+ *
+ * Errors: arguments are checked before anything is enqueued; a bad argument
+ * returns EDM_ERR_INVALID_ARG and enqueues nothing.  Launch failures return
+ * EDM_ERR_CUDA.  Conditions found on the device (an out-of-range E in a
+ * device array, a bounded wait that gave up) are recorded in the context and
+ * reported by edm_ctx_sync.  No call throws; no call aborts the process.
+ */
+#ifndef EDM_H
+#define EDM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum edm_status {
+    EDM_OK = 0,
+    EDM_ERR_INVALID_ARG = 1, /* an argument is out of range or NULL        */
+    EDM_ERR_CUDA = 2,        /* a CUDA runtime call or launch failed       */
+    EDM_ERR_OOM = 3,         /* workspace allocation failed                */
+    EDM_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up         */
+    EDM_ERR_INTERNAL = 5     /* an internal consistency check failed       */
+} edm_status;
+
+/* Storage of the target series inside edm_ccm_all.  Library distances,
+ * weights and the Pearson moments are FP32 in both modes. */
+typedef enum edm_precision {
+    EDM_FP32 = 0,         /* targets stored as float32                  */
+    EDM_BF16_TARGETS = 1  /* targets stored as bfloat16 (half the bytes) */
+} edm_precision;
+
+enum {
+    EDM_E_MAX = 20, /* largest embedding dimension accepted             */
+    EDM_K_MAX = 24, /* largest neighbour count accepted by edm_knn      */
+    EDM_L_MAX = 65535 /* longest series (neighbour indices are 16-bit)  */
+};
+
+typedef struct edm_ctx edm_ctx;
+
+/* Create a context on CUDA device `device`, enqueuing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context.  Returns EDM_ERR_CUDA when no such device exists. */
+edm_status edm_create(edm_ctx **out, int device, void *cuda_stream);
+
+/* Synchronise the context's stream and free its workspace and itself. */
+edm_status edm_destroy(edm_ctx *ctx);
+
+/* Enqueue subsequent calls on `cuda_stream` (a cudaStream_t). */
+edm_status edm_set_stream(edm_ctx *ctx, void *cuda_stream);
+
+/* Block until the context's stream is idle; return (and clear) the first
+ * device-side error recorded since the previous edm_ctx_sync. */
+edm_status edm_ctx_sync(edm_ctx *ctx);
+
+/* Static English text for a status code. */
+const char *edm_status_string(edm_status s);
+
+/* Detail of the last host-side error of this context (static buffer owned by
+ * the context; empty when none). */
+const char *edm_last_error(edm_ctx *ctx);
+
+/* Number of kernels libedm has launched through this context. */
+uint64_t edm_kernel_launches(edm_ctx *ctx);
+
+/* Measurement aids (no counterpart in the paper).
+ * edm_profile_enable(ctx, 1) clears the record and times every kernel this
+ * context launches from then on with CUDA events on its stream; 0 stops.
+ * edm_profile_read synchronises the stream and returns, for the kernels
+ * whose name equals `kernel` (e.g. "lookup_kernel"), the summed device time
+ * in milliseconds and the number of launches. */
+edm_status edm_profile_enable(edm_ctx *ctx, int on);
+edm_status edm_profile_read(edm_ctx *ctx, const char *kernel, double *total_ms,
+                            int *launches);
+
+/* Shared-memory gather bandwidth of this GPU in bytes/s, the roofline of the
+ * lookup kernel: every SM runs warps that read whole 128-byte rows of a
+ * shared-memory tile at data-dependent row indexes (the lookup's access
+ * pattern, one conflict-free wavefront per read) for about `ms` ms. */
+edm_status edm_probe_smem_bandwidth(edm_ctx *ctx, double ms, double *bytes_per_s);
+
+/* Section 2.1 step 1: time-delay embedding of one series.
+ * x [L] float32; out [L-(E-1)tau][E] float32, row i = time (E-1)tau+i,
+ * column l = x[t - l*tau].  1 <= E <= EDM_E_MAX, tau >= 1, (E-1)tau < L. */
+edm_status edm_embed(edm_ctx *ctx, const float *x, int L, int E, int tau,
+                     float *out);
+
+/* Section 2.1 step 2 (and Algorithms 1-2): exhaustive all-kNN of N series.
+ * X [N][L] float32.  For each series and each point t in P, the k nearest
+ * points of P\{t}, ascending by (squared distance, time index).
+ * idx  [N][n][k] int32: the neighbour's time index u (not shifted by Tp);
+ * dist [N][n][k] float32: the Euclidean distance, i.e. the FP64 square root
+ * of the FP64 squared distance, rounded to float32.  dist may be NULL.
+ * 1 <= E <= EDM_E_MAX, tau >= 1, Tp >= 0, 1 <= k <= EDM_K_MAX, k <= n-1,
+ * 2 <= L <= EDM_L_MAX, N >= 1. */
+edm_status edm_knn(edm_ctx *ctx, const float *X, int N, int L, int E, int tau,
+                   int Tp, int k, int32_t *idx, float *dist);
+
+/* Optimal embedding dimension per series (named in section 3.3; the method
+ * is leave-one-out simplex projection of the series onto itself at horizon
+ * Tp_sel, E = 1..E_max).  X [N][L] float32.
+ * E_opt [N] int32: argmax_E rho_E (NaN ranks below every number, ties go
+ * to the smaller E; 1 when every rho_E is NaN).
+ * rho_E [N][E_max] float32 or NULL: the skill of every E (NaN when E leaves
+ * fewer than E+2 points).  1 <= E_max <= EDM_E_MAX, tau >= 1, Tp_sel >= 0. */
+edm_status edm_simplex_optimal_E(edm_ctx *ctx, const float *X, int N, int L,
+                                 int E_max, int tau, int Tp_sel,
+                                 int32_t *E_opt, float *rho_E);
+
+/* Section 2.1 steps 1-4 for every (library, target) pair (pairwise CCM,
+ * section 3.3 "Lookup").  X_lib [N_lib][L], Y_tgt [N_tgt][L] float32 (they
+ * may be the same array).  E_lib [N_lib] int32 on the device: the embedding
+ * dimension of each library (1..EDM_E_MAX; a value out of range, or one that
+ * leaves fewer than E+2 points, gives a row of NaN and EDM_ERR_INVALID_ARG
+ * from the next edm_ctx_sync).
+ * rho [N_lib][N_tgt] float32 row-major: rho[i][j] = Pearson skill of library
+ * i's manifold predicting target j; high means "target j CCM-causes library
+ * i".  prec selects the storage of the targets. */
+edm_status edm_ccm_all(edm_ctx *ctx, const float *X_lib, int N_lib,
+                       const float *Y_tgt, int N_tgt, int L,
+                       const int32_t *E_lib, int tau, int Tp,
+                       edm_precision prec, float *rho);
+
+/* One all-to-all CCM problem inside a batch: the series X [N][L] are both
+ * the libraries and the targets; only the library rows lib_begin..lib_end-1
+ * are computed (so a problem can be split or resumed by row block).
+ * E_lib [N] int32 (device); rho [lib_end-lib_begin][N] float32 (device). */
+typedef struct edm_instance {
+    const float *X;
+    int N;
+    int L;
+    const int32_t *E_lib;
+    int tau;
+    int Tp;
+    float *rho;
+    int lib_begin;
+    int lib_end;
+} edm_instance;
+
+/* Run n_inst independent CCM problems of uneven N and L.  `inst` is a HOST
+ * array of n_inst descriptors (read before the call returns); the pointers
+ * inside are device pointers.  Same per-instance rules as edm_ccm_all. */
+edm_status edm_ccm_batched(edm_ctx *ctx, const edm_instance *inst, int n_inst,
+                           edm_precision prec);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EDM_H */

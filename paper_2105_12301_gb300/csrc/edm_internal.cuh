@@ -1,0 +1,209 @@
+// edm_internal.cuh -- shared host/device definitions of libedm (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/edm.h"
+
+struct edm_prof_rec {
+    const char *kernel;
+    cudaEvent_t start, stop;
+};
+
+struct edm_ctx {
+    int device;
+    cudaStream_t stream;
+    int num_sms;
+    int max_smem_optin;        // bytes of dynamic shared memory a CTA may opt into
+    void *ws;                  // workspace (neighbour tables, transposed targets, partials)
+    size_t ws_bytes;
+    int *d_flags;              // device-side error flags (EDMF_*)
+    uint64_t launches;         // kernels launched through this context
+    size_t table_budget;       // bytes of workspace a chunk of neighbour tables may use
+    char last_error[256];
+    bool prof_on;              // time every launch with CUDA events
+    cudaEvent_t prof_pending;  // start event of the launch in progress
+    std::vector<edm_prof_rec> prof;
+    std::vector<cudaEvent_t> prof_pool;
+};
+
+// device-side error flags, OR-ed into ctx->d_flags
+enum { EDMF_TIMEOUT = 1, EDMF_BADARG = 2, EDMF_INTERNAL = 4 };
+
+namespace edm {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int WARP = 32;
+
+// ---------------------------------------------------------------- host side
+
+edm_status set_error(edm_ctx *ctx, edm_status s, const char *fmt, ...);
+edm_status cuda_check(edm_ctx *ctx, cudaError_t e, const char *what);
+// Make sure the workspace holds at least `bytes`; returns its base.
+edm_status ws_reserve(edm_ctx *ctx, size_t bytes);
+// Call right before a kernel launch (records the start event when profiling).
+void before_launch(edm_ctx *ctx);
+// Record a kernel launch and check for a launch error.
+edm_status after_launch(edm_ctx *ctx, const char *kernel);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Layout of one row of a CCM neighbour table: k uint16 neighbour rows
+// (already shifted by Tp), padded to 16 bytes, then k float32 normalised
+// weights, padded to 16 bytes.
+__host__ __device__ inline int table_idx_bytes(int k) { return ((2 * k + 15) / 16) * 16; }
+__host__ __device__ inline int table_row_bytes(int k) {
+    return table_idx_bytes(k) + ((4 * k + 15) / 16) * 16;
+}
+
+// Launchers (one translation unit each).
+edm_status launch_embed(edm_ctx *ctx, const float *x, int L, int E, int tau, float *out);
+edm_status launch_knn(edm_ctx *ctx, const float *X, int N, int L, int E, int tau, int Tp,
+                      int k, int32_t *idx, float *dist);
+edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, int lib0, int nlib, int L,
+                             const int32_t *E_lib, int tau, int Tp, uint8_t *tables,
+                             size_t slot_bytes);
+edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max, int tau,
+                          int Tp_sel, int32_t *E_opt, float *rho_E);
+edm_status launch_target_store(edm_ctx *ctx, const float *Y, int N_tgt, int L,
+                               edm_precision prec, uint8_t *Yt, double *mean_ws);
+edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L,
+                         const uint8_t *tables, size_t slot_bytes, const int32_t *E_lib,
+                         int lib0, int nlib, int tau, int Tp, edm_precision prec,
+                         float *rho, long long rho_ld);
+edm_status launch_smem_probe(edm_ctx *ctx, double ms, double *bytes_per_s);
+size_t simplex_workspace_bytes(edm_ctx *ctx, int N, int L, int E_max);
+size_t ccm_slot_bytes(int L, int tau, int Tp);
+size_t target_store_bytes(int N_tgt, int L, edm_precision prec);
+
+// --------------------------------------------------------------- device side
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ void set_flag(int *flags, int f) {
+    if (flags) atomicOr(flags, f);
+}
+
+// Ascending bitonic sort of one 64-bit key per lane; returns the key at
+// position r (broadcast to every lane).
+__device__ __forceinline__ uint64_t warp_sorted_at(uint64_t key, int r) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            uint64_t other = __shfl_xor_sync(FULL, key, j);
+            bool up = (lane & k) == 0;
+            bool lower = (lane & j) == 0;
+            uint64_t lo = key < other ? key : other;
+            uint64_t hi = key < other ? other : key;
+            key = (lower == up) ? lo : hi;
+        }
+    }
+    return __shfl_sync(FULL, key, r);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Pearson's rho from the five raw moments of n pairs (a, b), in FP64.
+// A variance that is not positive gives NaN.
+__device__ __forceinline__ double pearson_from_moments(double n, double sa, double sb,
+                                                       double saa, double sbb, double sab) {
+    double va = saa - sa * sa / n;
+    double vb = sbb - sb * sb / n;
+    double cv = sab - sa * sb / n;
+    if (!(va > 0.0) || !(vb > 0.0)) return __longlong_as_double(0x7ff8000000000000LL);
+    return cv / sqrt(va * vb);
+}
+
+// ------------------------------------------------ mbarrier + bulk copy (PTX)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase with the given parity to complete, for at most about
+// two seconds.  On timeout the context's error flag is raised and false is
+// returned; the caller carries on (its data is then garbage) so that every
+// thread still reaches every later barrier and the kernel always ends.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *flags) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > 2000000000ull) {
+            set_flag(flags, EDMF_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// 1-D bulk copy global -> this CTA's shared memory, completing on `bar`.
+// dst and src must be 16-byte aligned and bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+}  // namespace edm

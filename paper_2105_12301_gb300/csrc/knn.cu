@@ -1,0 +1,223 @@
+// knn.cu -- time-delay embedding and exhaustive all-kNN (kEDM section 2.1
+// steps 1-3, Algorithms 1 and 2).
+//
+// One CTA holds one series in shared memory (the paper's "team scratch"
+// caching of x) and a block of its query rows; one warp per query row runs
+// knn_row (knn_core.cuh).  Embedding is fused: lagged values are read from
+// the staged series, the embedded points are never written.
+#include "knn_core.cuh"
+
+namespace edm {
+
+constexpr int KNN_WARPS = 8;
+constexpr int SERIES_SMEM_MAX = 96 * 1024;  // stage the series when it fits
+
+// ------------------------------------------------------------------ embed
+
+__global__ void embed_kernel(const float *__restrict__ x, int L, int E, int tau,
+                             float *__restrict__ out) {
+    const int n = L - (E - 1) * tau;
+    const long long total = static_cast<long long>(n) * E;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int row = static_cast<int>(i / E), l = static_cast<int>(i % E);
+        out[i] = x[(E - 1) * tau + row - l * tau];
+    }
+}
+
+edm_status launch_embed(edm_ctx *ctx, const float *x, int L, int E, int tau, float *out) {
+    const long long total = static_cast<long long>(L - (E - 1) * tau) * E;
+    const int blocks = static_cast<int>(std::min<long long>((total + 255) / 256, 4LL * ctx->num_sms));
+    before_launch(ctx);
+    embed_kernel<<<blocks, 256, 0, ctx->stream>>>(x, L, E, tau, out);
+    return after_launch(ctx, "embed_kernel");
+}
+
+// ------------------------------------------------------- series staging
+
+// Copy the series into shared memory when it fits (SMEM), else read it from
+// global memory through L1.  Returns the pointer the rows read from.
+template <bool SMEM>
+__device__ __forceinline__ const float *stage_series(const float *xg, int L, float *xs_s) {
+    if constexpr (!SMEM) {
+        return xg;
+    } else {
+        for (int i = threadIdx.x; i < L; i += blockDim.x) xs_s[i] = xg[i];
+        __syncthreads();
+        return xs_s;
+    }
+}
+
+static size_t knn_smem_bytes(bool smem_series, int L) {
+    return KNN_WARPS * sizeof(WarpScratch) + (smem_series ? align_up(sizeof(float) * L, 16) : 0);
+}
+
+// Rows per CTA: enough CTAs to fill the GPU several times over.
+static int rows_per_cta(edm_ctx *ctx, int N, int n) {
+    const long long want_ctas = 8LL * ctx->num_sms;
+    long long blocks_per_series = (want_ctas + N - 1) / N;
+    int rb = static_cast<int>((n + blocks_per_series - 1) / blocks_per_series);
+    rb = std::max(rb, 4 * KNN_WARPS);
+    return std::min(rb, n);
+}
+
+// ---------------------------------------------------------------- edm_knn
+
+template <int E, bool SMEM>
+__global__ void __launch_bounds__(KNN_WARPS * 32)
+    knn_out_kernel(const float *__restrict__ X, int L, int tau, int Tp, int K, int RB,
+                   int32_t *__restrict__ idx, float *__restrict__ dist) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    WarpScratch *wsa = reinterpret_cast<WarpScratch *>(smem);
+    float *xs_s = reinterpret_cast<float *>(smem + KNN_WARPS * sizeof(WarpScratch));
+    const int series = blockIdx.x;
+    const float *xs = stage_series<SMEM>(X + static_cast<size_t>(series) * L, L, xs_s);
+    const int lo = (E - 1) * tau, hi = L - 1 - Tp, n = hi - lo + 1;
+    const int r0 = blockIdx.y * RB, r1 = min(n, r0 + RB);
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    WarpScratch *ws = wsa + warp;
+    for (int i = r0 + warp; i < r1; i += KNN_WARPS) {
+        int u = 0;
+        float d = 0.f;
+        knn_row<E, KNN_ORDERED>(xs, lo + i, lo, hi, tau, K, ws, &u, &d);
+        const size_t o = (static_cast<size_t>(series) * n + i) * K;
+        if (lane < K) {
+            idx[o + lane] = u;
+            if (dist) dist[o + lane] = d;
+        }
+    }
+}
+
+template <int E>
+static edm_status launch_knn_E(edm_ctx *ctx, const float *X, int N, int L, int tau, int Tp, int K,
+                               int32_t *idx, float *dist) {
+    const int n = L - (E - 1) * tau - Tp;
+    const int RB = rows_per_cta(ctx, N, n);
+    dim3 grid(N, (n + RB - 1) / RB);
+    const bool smem_series = sizeof(float) * static_cast<size_t>(L) <= SERIES_SMEM_MAX;
+    const size_t smem = knn_smem_bytes(smem_series, L);
+    if (smem_series) {
+        auto kern = knn_out_kernel<E, true>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        before_launch(ctx);
+        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, L, tau, Tp, K, RB, idx, dist);
+    } else {
+        auto kern = knn_out_kernel<E, false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        before_launch(ctx);
+        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, L, tau, Tp, K, RB, idx, dist);
+    }
+    return after_launch(ctx, "knn_out_kernel");
+}
+
+edm_status launch_knn(edm_ctx *ctx, const float *X, int N, int L, int E, int tau, int Tp, int k,
+                      int32_t *idx, float *dist) {
+    switch (E) {
+#define EDM_CASE(e) \
+    case e: return launch_knn_E<e>(ctx, X, N, L, tau, Tp, k, idx, dist);
+        EDM_CASE(1) EDM_CASE(2) EDM_CASE(3) EDM_CASE(4) EDM_CASE(5) EDM_CASE(6) EDM_CASE(7)
+        EDM_CASE(8) EDM_CASE(9) EDM_CASE(10) EDM_CASE(11) EDM_CASE(12) EDM_CASE(13)
+        EDM_CASE(14) EDM_CASE(15) EDM_CASE(16) EDM_CASE(17) EDM_CASE(18) EDM_CASE(19)
+        EDM_CASE(20)
+#undef EDM_CASE
+    default: return set_error(ctx, EDM_ERR_INVALID_ARG, "E=%d out of range", E);
+    }
+}
+
+// ----------------------------------------------------- CCM neighbour tables
+
+// Rows [r0, r1) of one library's table: exact neighbours, normalised simplex
+// weights, neighbour rows pre-shifted by Tp.
+template <int E>
+__device__ __forceinline__ void table_rows(const float *xs, int L, int tau, int Tp, int r0, int r1,
+                                           WarpScratch *ws, uint8_t *slot) {
+    constexpr int K = E + 1;
+    constexpr int IB = (2 * K + 15) / 16 * 16;
+    constexpr int WN = (4 * K + 15) / 16 * 4;  // weight entries incl. padding
+    constexpr int RS = IB + WN * 4;
+    const int lo = (E - 1) * tau, hi = L - 1 - Tp;
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    for (int i = r0 + warp; i < r1; i += KNN_WARPS) {
+        int u = 0;
+        float d = 0.f;
+        knn_row<E, KNN_ORDERED>(xs, lo + i, lo, hi, tau, K, ws, &u, &d);
+        const float w = simplex_weight(d, K);
+        uint8_t *row = slot + static_cast<size_t>(i) * RS;
+        uint16_t *ri = reinterpret_cast<uint16_t *>(row);
+        float *rw = reinterpret_cast<float *>(row + IB);
+        if (lane < IB / 2) ri[lane] = lane < K ? static_cast<uint16_t>(u + Tp) : 0;
+        if (lane < WN) rw[lane] = lane < K ? w : 0.f;
+    }
+}
+
+__host__ __device__ inline bool ccm_E_valid(int E, int L, int tau, int Tp) {
+    return E >= 1 && E <= EDM_E_MAX && L - (E - 1) * tau - Tp >= E + 2;
+}
+
+template <bool SMEM>
+__global__ void __launch_bounds__(KNN_WARPS * 32)
+    ccm_table_kernel(const float *__restrict__ X, int lib0, int L, const int32_t *__restrict__ E_lib,
+                     int tau, int Tp, int RB, uint8_t *__restrict__ tables, size_t slot_bytes,
+                     int *flags) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    WarpScratch *wsa = reinterpret_cast<WarpScratch *>(smem);
+    float *xs_s = reinterpret_cast<float *>(smem + KNN_WARPS * sizeof(WarpScratch));
+    const int lib = lib0 + blockIdx.x;
+    const int E = E_lib[lib];
+    if (!ccm_E_valid(E, L, tau, Tp)) {
+        if (blockIdx.y == 0 && threadIdx.x == 0) set_flag(flags, EDMF_BADARG);
+        return;
+    }
+    const int n = L - (E - 1) * tau - Tp;
+    const int r0 = blockIdx.y * RB, r1 = min(n, r0 + RB);
+    if (r0 >= r1) return;
+    const float *xs = stage_series<SMEM>(X + static_cast<size_t>(lib) * L, L, xs_s);
+    WarpScratch *ws = wsa + (threadIdx.x >> 5);
+    uint8_t *slot = tables + static_cast<size_t>(blockIdx.x) * slot_bytes;
+    switch (E) {
+#define EDM_CASE(e) \
+    case e: table_rows<e>(xs, L, tau, Tp, r0, r1, ws, slot); break;
+        EDM_CASE(1) EDM_CASE(2) EDM_CASE(3) EDM_CASE(4) EDM_CASE(5) EDM_CASE(6) EDM_CASE(7)
+        EDM_CASE(8) EDM_CASE(9) EDM_CASE(10) EDM_CASE(11) EDM_CASE(12) EDM_CASE(13)
+        EDM_CASE(14) EDM_CASE(15) EDM_CASE(16) EDM_CASE(17) EDM_CASE(18) EDM_CASE(19)
+        EDM_CASE(20)
+#undef EDM_CASE
+    default: break;
+    }
+}
+
+size_t ccm_slot_bytes(int L, int tau, int Tp) {
+    size_t best = 0;
+    for (int E = 1; E <= EDM_E_MAX; ++E) {
+        const int n = L - (E - 1) * tau - Tp;
+        if (n < 1) break;
+        best = std::max(best, static_cast<size_t>(n) * table_row_bytes(E + 1));
+    }
+    return align_up(best, 256);
+}
+
+edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, int lib0, int nlib, int L,
+                             const int32_t *E_lib, int tau, int Tp, uint8_t *tables,
+                             size_t slot_bytes) {
+    const int n_max = L - Tp;  // rows at E = 1, the most of any E
+    const int RB = rows_per_cta(ctx, nlib, n_max);
+    dim3 grid(nlib, (n_max + RB - 1) / RB);
+    const bool smem_series = sizeof(float) * static_cast<size_t>(L) <= SERIES_SMEM_MAX;
+    const size_t smem = knn_smem_bytes(smem_series, L);
+    if (smem_series) {
+        auto kern = ccm_table_kernel<true>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        before_launch(ctx);
+        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, lib0, L, E_lib, tau, Tp, RB, tables,
+                                                          slot_bytes, ctx->d_flags);
+    } else {
+        auto kern = ccm_table_kernel<false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        before_launch(ctx);
+        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, lib0, L, E_lib, tau, Tp, RB, tables,
+                                                          slot_bytes, ctx->d_flags);
+    }
+    return after_launch(ctx, "ccm_table_kernel");
+}
+
+}  // namespace edm

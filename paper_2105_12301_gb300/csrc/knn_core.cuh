@@ -1,0 +1,314 @@
+// knn_core.cuh -- one warp finds the k nearest neighbours of one query point.
+//
+// kEDM section 2.1 step 2 and Algorithms 1-2: exhaustive distances from the
+// query x(t) to every other library point (the embedding is never
+// materialised: lagged values are read straight from the series), then the
+// k smallest.  Instead of Algorithm 2's per-thread priority queues in shared
+// memory, a warp
+//   1. takes the minimum key (s, u) of each lane's candidates; the R-th
+//      smallest of those 32 minima bounds the R-th smallest key of the row;
+//   2. collects every key at or below that bound into a small per-warp
+//      buffer (typically R..2R entries) and ranks them;
+//   3. makes the FP32 ranking exact against an FP64 evaluation of the same
+//      definition: every candidate whose FP64 key can belong to the k
+//      nearest has an FP32 squared distance within the band
+//      s32 <= s32_(k) (1 + 4 (E+3) 2^-24) + 3 * 2^-140
+//      (|s32 - s| <= (E+2) u s for u = 2^-24 plus an absolute term for
+//      subnormal squares, and the same for FP64 with u = 2^-53).  If the
+//      collected candidates cover that band, ranking them by the FP64 key
+//      (s64, u) gives exactly the FP64 neighbour set and order; otherwise
+//      the band is collected and ranked in FP64, and in a degenerate row
+//      (more than CAP candidates in the band) k FP64 arg-min sweeps are run.
+// The FP64 squared distance uses the same operations in the same order as
+// the definition: d = (double)a - (double)b, s = fma(d, d, s), l = 0..E-1.
+#pragma once
+
+#include "edm_internal.cuh"
+
+namespace edm {
+
+constexpr int KNN_CAP = 128;     // per-warp candidate buffer
+constexpr int KNN_MARGIN = 8;    // extra FP32 candidates re-ranked in FP64
+
+struct WarpScratch {
+    uint64_t key[KNN_CAP];   // collected FP32 keys
+    double s64[KNN_CAP];     // their FP64 squared distances (band fallback)
+    uint64_t sel[32];        // the R smallest collected keys, ascending
+    double sel_s64[32];      // exact ranking: FP64 distances by final rank
+    int sel_u[32];
+    int count;
+    int pad;
+};
+
+enum KnnMode { KNN_SET = 0, KNN_ORDERED = 1 };
+
+// Flags returned by knn_row (for statistics only).
+enum { KNN_USED_BAND = 1, KNN_USED_BRUTE = 2 };
+
+__device__ __forceinline__ uint64_t mk_key(float s, int u) {
+    return (static_cast<uint64_t>(__float_as_uint(s)) << 32) | static_cast<uint32_t>(u);
+}
+__device__ __forceinline__ float key_s(uint64_t k) {
+    return __uint_as_float(static_cast<uint32_t>(k >> 32));
+}
+__device__ __forceinline__ int key_u(uint64_t k) { return static_cast<int>(static_cast<uint32_t>(k)); }
+
+// FP32 squared distance between query (held in q) and the point at time u,
+// lag order 0..E-1, one fma per lag.
+template <int E>
+__device__ __forceinline__ float dist32(const float (&q)[E], const float *xs, int u, int tau) {
+    float s = 0.f;
+#pragma unroll
+    for (int l = 0; l < E; ++l) {
+        float d = __fsub_rn(q[l], xs[u - l * tau]);
+        s = __fmaf_rn(d, d, s);
+    }
+    return s;
+}
+
+// FP64 squared distance, same operation sequence as the definition.
+__device__ __forceinline__ double dist64(const float *xs, int t, int u, int E, int tau) {
+    double s = 0.0;
+    for (int l = 0; l < E; ++l) {
+        double d = __dsub_rn(static_cast<double>(xs[t - l * tau]),
+                             static_cast<double>(xs[u - l * tau]));
+        s = __fma_rn(d, d, s);
+    }
+    return s;
+}
+
+// Upper edge of the band of FP32 squared distances that may hide an FP64
+// neighbour, given the k-th smallest FP32 squared distance sK.
+__device__ __forceinline__ float band_edge(float sK, int E) {
+    double thr = static_cast<double>(sK) * (1.0 + 4.0 * (E + 3) * 0x1p-24) + 3.0 * 0x1p-140;
+    return __double2float_ru(thr);
+}
+
+__device__ __forceinline__ bool less64(double sa, int ua, double sb, int ub) {
+    return sa < sb || (sa == sb && ua < ub);
+}
+
+// Collect into ws->key every candidate key <= theta (at most KNN_CAP kept);
+// returns how many there are in total.
+template <int E>
+__device__ __forceinline__ int filter_keys(const float (&q)[E], const float *xs, int t, int lo,
+                                           int hi, int tau, uint64_t theta, WarpScratch *ws) {
+    const int lane = lane_id();
+    if (lane == 0) ws->count = 0;
+    __syncwarp();
+    for (int u = lo + lane; u <= hi; u += WARP) {
+        if (u == t) continue;
+        uint64_t key = mk_key(dist32<E>(q, xs, u, tau), u);
+        if (key <= theta) {
+            int pos = atomicAdd(&ws->count, 1);
+            if (pos < KNN_CAP) ws->key[pos] = key;
+        }
+    }
+    __syncwarp();
+    int c = ws->count;
+    __syncwarp();
+    return c;
+}
+
+// Rank the c (<= KNN_CAP) keys of ws->key; write the R smallest, ascending,
+// to ws->sel.
+__device__ __forceinline__ void rank_keys(WarpScratch *ws, int c, int R) {
+    const int lane = lane_id();
+    for (int e = lane; e < c; e += WARP) {
+        uint64_t ke = ws->key[e];
+        int rank = 0;
+        for (int e2 = 0; e2 < c; ++e2) rank += ws->key[e2] < ke;
+        if (rank < R) ws->sel[rank] = ke;
+    }
+    __syncwarp();
+}
+
+// The key of rank r among the first c keys of ws->key (all lanes).
+__device__ __forceinline__ uint64_t key_at_rank(WarpScratch *ws, int c, int r) {
+    const int lane = lane_id();
+    for (int e = lane; e < c; e += WARP) {
+        uint64_t ke = ws->key[e];
+        int rank = 0;
+        for (int e2 = 0; e2 < c; ++e2) rank += ws->key[e2] < ke;
+        if (rank == r) ws->sel[0] = ke;
+    }
+    __syncwarp();
+    uint64_t v = ws->sel[0];
+    __syncwarp();
+    return v;
+}
+
+// Exact ranking of the c band candidates collected in ws->key by their FP64
+// key; the K smallest go to ws->sel_u / ws->sel_s64 in order.
+__device__ __forceinline__ void rank_band_fp64(const float *xs, int t, int E, int tau,
+                                               WarpScratch *ws, int c, int K) {
+    const int lane = lane_id();
+    for (int e = lane; e < c; e += WARP) ws->s64[e] = dist64(xs, t, key_u(ws->key[e]), E, tau);
+    __syncwarp();
+    for (int e = lane; e < c; e += WARP) {
+        double se = ws->s64[e];
+        int ue = key_u(ws->key[e]);
+        int rank = 0;
+        for (int e2 = 0; e2 < c; ++e2) rank += less64(ws->s64[e2], key_u(ws->key[e2]), se, ue);
+        if (rank < K) {
+            ws->sel_s64[rank] = se;
+            ws->sel_u[rank] = ue;
+        }
+    }
+    __syncwarp();
+}
+
+// Degenerate rows: K sweeps, each taking the smallest FP64 key above the
+// previous one.  O(K n E) FP64 work; only reached when more than KNN_CAP
+// candidates fall in the band (long runs of repeated values).
+static __device__ __noinline__ void brute_fp64(const float *xs, int t, int lo, int hi, int E, int tau,
+                                        WarpScratch *ws, int K) {
+    const int lane = lane_id();
+    double last_s = -1.0;
+    int last_u = -1;
+    for (int r = 0; r < K; ++r) {
+        double best_s = __longlong_as_double(0x7ff0000000000000LL);
+        int best_u = 0x7fffffff;
+        for (int u = lo + lane; u <= hi; u += WARP) {
+            if (u == t) continue;
+            double s = dist64(xs, t, u, E, tau);
+            if (less64(last_s, last_u, s, u) && less64(s, u, best_s, best_u)) {
+                best_s = s;
+                best_u = u;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double os = __shfl_xor_sync(FULL, best_s, o);
+            int ou = __shfl_xor_sync(FULL, best_u, o);
+            if (less64(os, ou, best_s, best_u)) {
+                best_s = os;
+                best_u = ou;
+            }
+        }
+        if (lane == 0) {
+            ws->sel_s64[r] = best_s;
+            ws->sel_u[r] = best_u;
+        }
+        last_s = best_s;
+        last_u = best_u;
+    }
+    __syncwarp();
+}
+
+// The K nearest neighbours of the point at time t among the times lo..hi
+// (t excluded).  Requires 1 <= K <= hi-lo and K + KNN_MARGIN <= 32 in
+// KNN_ORDERED mode, K + 1 <= 32 in KNN_SET mode.  All lanes of the warp call
+// it; on return lane r < K holds the r-th neighbour:
+//   KNN_ORDERED: exact FP64 order (s64, u); d = (float)sqrt(s64).
+//   KNN_SET:     the exact FP64 neighbour set; order and d from FP32 (the
+//                exact FP64 values when the band had to be resolved).
+// Returns KNN_USED_* flags.
+template <int E, int MODE>
+__device__ int knn_row(const float *xs, int t, int lo, int hi, int tau, int K, WarpScratch *ws,
+                       int *out_u, float *out_d) {
+    const int lane = lane_id();
+    float q[E];
+#pragma unroll
+    for (int l = 0; l < E; ++l) q[l] = xs[t - l * tau];
+
+    const int nc = hi - lo;  // number of candidates (the point itself excluded)
+    const int R = (MODE == KNN_ORDERED) ? min(K + KNN_MARGIN, nc) : min(K + 1, nc);
+
+    // 1. per-lane minimum key, then the R-th smallest of the 32 minima
+    uint64_t kmin = ~0ull;
+    for (int u = lo + lane; u <= hi; u += WARP) {
+        if (u == t) continue;
+        uint64_t key = mk_key(dist32<E>(q, xs, u, tau), u);
+        kmin = key < kmin ? key : kmin;
+    }
+    uint64_t theta = warp_sorted_at(kmin, R - 1);
+
+    // 2. collect keys <= theta; shrink theta while the buffer overflows
+    int c = filter_keys<E>(q, xs, t, lo, hi, tau, theta, ws);
+    while (c > KNN_CAP) {
+        theta = key_at_rank(ws, KNN_CAP, R - 1);
+        c = filter_keys<E>(q, xs, t, lo, hi, tau, theta, ws);
+    }
+    rank_keys(ws, c, R);  // ws->sel[0..R) ascending FP32 keys
+
+    const float sK = key_s(ws->sel[K - 1]);
+    const float edge = band_edge(sK, E);
+    const bool all_taken = (R == nc);
+
+    if (MODE == KNN_SET) {
+        // exact set when the (K+1)-th FP32 key lies beyond the band
+        if (R <= K || key_s(ws->sel[K]) > edge) {
+            if (lane < K) {
+                uint64_t k = ws->sel[lane];
+                *out_u = key_u(k);
+                *out_d = sqrtf(key_s(k));
+            }
+            __syncwarp();
+            return 0;
+        }
+    } else {
+        // FP64 re-rank of the R collected keys; valid when they cover the band
+        if (all_taken || key_s(ws->sel[R - 1]) > edge) {
+            double s64 = __longlong_as_double(0x7ff0000000000000LL);
+            int u = 0x7fffffff;
+            if (lane < R) {
+                u = key_u(ws->sel[lane]);
+                s64 = dist64(xs, t, u, E, tau);
+            }
+            int rank = 0;
+            for (int j = 0; j < R; ++j) {
+                double sj = __shfl_sync(FULL, s64, j);
+                int uj = __shfl_sync(FULL, u, j);
+                rank += less64(sj, uj, s64, u);
+            }
+            if (lane < R && rank < K) {
+                ws->sel_s64[rank] = s64;
+                ws->sel_u[rank] = u;
+            }
+            __syncwarp();
+            if (lane < K) {
+                *out_u = ws->sel_u[lane];
+                *out_d = __double2float_rn(__dsqrt_rn(ws->sel_s64[lane]));
+            }
+            __syncwarp();
+            return 0;
+        }
+    }
+
+    // 3. band fallback: every candidate with s32 <= edge, ranked in FP64
+    int flags = KNN_USED_BAND;
+    c = filter_keys<E>(q, xs, t, lo, hi, tau, mk_key(edge, 0x7fffffff), ws);
+    if (c <= KNN_CAP) {
+        rank_band_fp64(xs, t, E, tau, ws, c, K);
+    } else {
+        brute_fp64(xs, t, lo, hi, E, tau, ws, K);
+        flags |= KNN_USED_BRUTE;
+    }
+    if (lane < K) {
+        *out_u = ws->sel_u[lane];
+        *out_d = __double2float_rn(__dsqrt_rn(ws->sel_s64[lane]));
+    }
+    __syncwarp();
+    return flags;
+}
+
+// Simplex weights of the K neighbours held one per lane (lane r < K holds
+// distance d of rank r; lane 0 the nearest): w = exp(-d/d1) normalised, or
+// the d1 == 0 limit.  Returns the normalised weight of this lane (0 for
+// lanes >= K).
+__device__ __forceinline__ float simplex_weight(float d, int K) {
+    const int lane = lane_id();
+    const float d1 = __shfl_sync(FULL, d, 0);
+    float w = 0.f;
+    if (lane < K) {
+        if (d1 > 0.f)
+            w = expf(-(d / d1));
+        else
+            w = (d == 0.f) ? 1.f : 0.f;
+    }
+    const float sum = warp_sum(w);
+    return w / sum;
+}
+
+}  // namespace edm

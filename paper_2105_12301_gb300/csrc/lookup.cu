@@ -1,0 +1,384 @@
+// lookup.cu -- batched lookup with on-the-fly Pearson (kEDM section 2.1
+// steps 3-4, Algorithm 3 and the closing paragraph of section 3.3).
+//
+// Targets are first stored transposed and centred, in tiles of 32 (FP32) or
+// 64 (BF16) targets: Yt[tile][u][lane], one 128-byte row per time u.  One
+// CTA owns one target tile (staged in shared memory by a bulk TMA copy) and
+// a block of libraries.  A producer warp streams the libraries' neighbour
+// tables through a ring of shared-memory stages (bulk TMA copies completing
+// on mbarriers); eight consumer warps take one table row (one query time) at
+// a time: the k (neighbour row, weight) pairs are warp-uniform broadcast
+// reads, and lane l gathers target l's value at each neighbour row -- all
+// 32 lanes read one 128-byte shared-memory row, so every gather is a single
+// conflict-free wavefront.  The prediction never leaves registers; each lane
+// accumulates the five Pearson moments of its target in FP32, the CTA sums
+// the warps' partials in FP64 and writes rho.
+#include <cuda_bf16.h>
+
+#include "edm_internal.cuh"
+
+namespace edm {
+
+constexpr int LK_NW = 8;                       // consumer warps
+constexpr int LK_THREADS = (LK_NW + 1) * 32;   // + one producer warp
+constexpr int LK_CR = 32;                      // table rows per stage
+constexpr int LK_MAX_STAGES = 8;
+constexpr int LK_TILE_ROW = 128;               // bytes per time row of a tile
+
+// ---------------------------------------------------------- target store
+
+__global__ void target_mean_kernel(const float *__restrict__ Y, int N, int L,
+                                   double *__restrict__ mean) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = lane_id();
+    if (warp >= N) return;
+    const float *y = Y + static_cast<size_t>(warp) * L;
+    double s = 0.0;
+    for (int i = lane; i < L; i += 32) s += static_cast<double>(y[i]);
+    s = warp_sum_d(s);
+    if (lane == 0) mean[warp] = s / L;
+}
+
+// FP32: Yt[tile][u][32] = Y[32 tile + lane][u] - mean; pad targets are 0.
+// BF16: Yt[tile][u][64] bf16, lane l's 32-bit word holds targets 2l (low
+// half) and 2l+1 (high half), each rounded to nearest even.
+template <bool BF16>
+__global__ void target_store_kernel(const float *__restrict__ Y, int N, int L,
+                                    const double *__restrict__ mean, uint8_t *__restrict__ Yt) {
+    constexpr int TT = BF16 ? 64 : 32;  // targets per tile
+    __shared__ float s[TT][33];
+    const int tile = blockIdx.x, u0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int j = ty; j < TT; j += 8) {
+        const int tgt = tile * TT + j, u = u0 + tx;
+        float v = 0.f;
+        if (tgt < N && u < L)
+            v = static_cast<float>(static_cast<double>(Y[static_cast<size_t>(tgt) * L + u]) -
+                                   mean[tgt]);
+        s[j][tx] = v;
+    }
+    __syncthreads();
+    uint8_t *base = Yt + static_cast<size_t>(tile) * L * LK_TILE_ROW;
+    for (int r = ty; r < 32; r += 8) {
+        const int u = u0 + r;
+        if (u >= L) continue;
+        if (BF16) {
+            const unsigned lo = __bfloat16_as_ushort(__float2bfloat16_rn(s[2 * tx][r]));
+            const unsigned hi = __bfloat16_as_ushort(__float2bfloat16_rn(s[2 * tx + 1][r]));
+            reinterpret_cast<uint32_t *>(base + static_cast<size_t>(u) * LK_TILE_ROW)[tx] =
+                lo | (hi << 16);
+        } else {
+            reinterpret_cast<float *>(base + static_cast<size_t>(u) * LK_TILE_ROW)[tx] = s[tx][r];
+        }
+    }
+}
+
+static int targets_per_tile(edm_precision prec) { return prec == EDM_BF16_TARGETS ? 64 : 32; }
+
+size_t target_store_bytes(int N_tgt, int L, edm_precision prec) {
+    const int tt = targets_per_tile(prec);
+    const size_t tiles = (N_tgt + tt - 1) / tt;
+    return align_up(tiles * L * LK_TILE_ROW, 256);
+}
+
+edm_status launch_target_store(edm_ctx *ctx, const float *Y, int N_tgt, int L,
+                               edm_precision prec, uint8_t *Yt, double *mean_ws) {
+    before_launch(ctx);
+    target_mean_kernel<<<(N_tgt * 32 + 255) / 256, 256, 0, ctx->stream>>>(Y, N_tgt, L, mean_ws);
+    edm_status st = after_launch(ctx, "target_mean_kernel");
+    if (st != EDM_OK) return st;
+    const int tt = targets_per_tile(prec);
+    dim3 grid((N_tgt + tt - 1) / tt, (L + 31) / 32), block(32, 8);
+    before_launch(ctx);
+    if (prec == EDM_BF16_TARGETS)
+        target_store_kernel<true><<<grid, block, 0, ctx->stream>>>(Y, N_tgt, L, mean_ws, Yt);
+    else
+        target_store_kernel<false><<<grid, block, 0, ctx->stream>>>(Y, N_tgt, L, mean_ws, Yt);
+    return after_launch(ctx, "target_store_kernel");
+}
+
+// ------------------------------------------------------- lookup + Pearson
+
+struct LookupArgs {
+    const uint8_t *Yt;
+    const uint8_t *tables;
+    size_t slot_bytes;
+    const int32_t *E_lib;  // indexed by library id
+    int lib0, nlib, LB;    // libraries [lib0, lib0+nlib) of this launch; LB per CTA
+    int L, tau, Tp, N_tgt;
+    int stages, stage_bytes;
+    float *rho;            // row of library lib0
+    long long rho_ld;
+    int *flags;
+};
+
+__device__ __forceinline__ bool lib_valid(int E, int L, int tau, int Tp) {
+    return E >= 1 && E <= EDM_E_MAX && L - (E - 1) * tau - Tp >= E + 2;
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+template <bool BF16>
+struct Moments {
+    static constexpr int N = BF16 ? 10 : 5;
+    float m[N];
+};
+
+// Gather + accumulate for one library whose k = K is a compile-time value.
+template <int K, bool BF16, bool SMEM_TILE>
+__device__ __forceinline__ void consume_library(const LookupArgs &a, const uint8_t *tile,
+                                                const uint8_t *stages, uint64_t *full,
+                                                uint64_t *empty, int &seq, int n, int t0,
+                                                float (&m)[Moments<BF16>::N]) {
+    constexpr int IB = (2 * K + 15) / 16 * 16;
+    constexpr int WN = (4 * K + 15) / 16 * 4;
+    constexpr int RS = IB + WN * 4;
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const uint32_t *tl = reinterpret_cast<const uint32_t *>(tile) + lane;
+    for (int c0 = 0; c0 < n; c0 += LK_CR) {
+        const int s = seq % a.stages;
+        const uint32_t par = (seq / a.stages) & 1;
+        mbar_wait_bounded(&full[s], par, a.flags);
+        const uint8_t *st = stages + static_cast<size_t>(s) * a.stage_bytes;
+        const int rows = min(LK_CR, n - c0);
+        for (int r = warp; r < rows; r += LK_NW) {
+            const uint8_t *row = st + r * RS;
+            uint32_t ix[(K + 1) / 2];
+            float w[WN];
+#pragma unroll
+            for (int q = 0; q < IB / 16; ++q) {
+                const uint4 v = reinterpret_cast<const uint4 *>(row)[q];
+                if (4 * q + 0 < (K + 1) / 2) ix[4 * q + 0] = v.x;
+                if (4 * q + 1 < (K + 1) / 2) ix[4 * q + 1] = v.y;
+                if (4 * q + 2 < (K + 1) / 2) ix[4 * q + 2] = v.z;
+                if (4 * q + 3 < (K + 1) / 2) ix[4 * q + 3] = v.w;
+            }
+#pragma unroll
+            for (int q = 0; q < WN / 4; ++q) {
+                const float4 v = reinterpret_cast<const float4 *>(row + IB)[q];
+                w[4 * q + 0] = v.x;
+                w[4 * q + 1] = v.y;
+                w[4 * q + 2] = v.z;
+                w[4 * q + 3] = v.w;
+            }
+            const int yrow = t0 + c0 + r + a.Tp;
+            if (!BF16) {
+                float acc = 0.f;
+#pragma unroll
+                for (int q = 0; q < K; ++q) {
+                    const uint32_t u = (q & 1) ? (ix[q >> 1] >> 16) : (ix[q >> 1] & 0xffffu);
+                    const float v = SMEM_TILE ? __uint_as_float(tl[u * 32])
+                                              : __uint_as_float(__ldg(tl + u * 32));
+                    acc = __fmaf_rn(w[q], v, acc);
+                }
+                const float y = SMEM_TILE ? __uint_as_float(tl[yrow * 32])
+                                          : __uint_as_float(__ldg(tl + yrow * 32));
+                m[0] += acc;
+                m[1] += y;
+                m[2] = __fmaf_rn(acc, acc, m[2]);
+                m[3] = __fmaf_rn(y, y, m[3]);
+                m[4] = __fmaf_rn(acc, y, m[4]);
+            } else {
+                float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+                for (int q = 0; q < K; ++q) {
+                    const uint32_t u = (q & 1) ? (ix[q >> 1] >> 16) : (ix[q >> 1] & 0xffffu);
+                    const uint32_t v = SMEM_TILE ? tl[u * 32] : __ldg(tl + u * 32);
+                    acc0 = __fmaf_rn(w[q], __uint_as_float(v << 16), acc0);
+                    acc1 = __fmaf_rn(w[q], __uint_as_float(v & 0xffff0000u), acc1);
+                }
+                const uint32_t yv = SMEM_TILE ? tl[yrow * 32] : __ldg(tl + yrow * 32);
+                const float y0 = __uint_as_float(yv << 16), y1 = __uint_as_float(yv & 0xffff0000u);
+                m[0] += acc0;
+                m[1] += y0;
+                m[2] = __fmaf_rn(acc0, acc0, m[2]);
+                m[3] = __fmaf_rn(y0, y0, m[3]);
+                m[4] = __fmaf_rn(acc0, y0, m[4]);
+                m[5] += acc1;
+                m[6] += y1;
+                m[7] = __fmaf_rn(acc1, acc1, m[7]);
+                m[8] = __fmaf_rn(y1, y1, m[8]);
+                m[9] = __fmaf_rn(acc1, y1, m[9]);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        ++seq;
+    }
+}
+
+template <bool BF16, bool SMEM_TILE>
+__global__ void __launch_bounds__(LK_THREADS, 1) lookup_kernel(const LookupArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    constexpr int NM = Moments<BF16>::N;
+    constexpr int TT = BF16 ? 64 : 32;
+    const int tile_id = blockIdx.x;
+    const int lb0 = a.lib0 + blockIdx.y * a.LB;
+    const int lb1 = min(a.lib0 + a.nlib, lb0 + a.LB);
+    const size_t tile_bytes = static_cast<size_t>(a.L) * LK_TILE_ROW;
+    const uint8_t *tile_g = a.Yt + static_cast<size_t>(tile_id) * tile_bytes;
+    uint8_t *tile_s = smem;
+    uint8_t *stages = smem + (SMEM_TILE ? tile_bytes : 0);
+    float *red = reinterpret_cast<float *>(stages + static_cast<size_t>(a.stages) * a.stage_bytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(red + 2 * LK_NW * NM * 32);
+    uint64_t *full = bars, *empty = bars + a.stages, *tbar = bars + 2 * a.stages;
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < a.stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], LK_NW);
+        }
+        mbar_init(tbar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    if (warp == LK_NW) {
+        // ---------------- producer: target tile, then the table stream
+        if (lane == 0) {
+            if (SMEM_TILE) {
+                mbar_arrive_expect_tx(tbar, static_cast<uint32_t>(tile_bytes));
+                for (size_t off = 0; off < tile_bytes; off += 32768)
+                    bulk_copy_g2s(tile_s + off, tile_g + off,
+                                  static_cast<uint32_t>(tile_bytes - off < 32768 ? tile_bytes - off : 32768), tbar);
+            }
+            int seq = 0;
+            for (int lib = lb0; lib < lb1; ++lib) {
+                const int E = a.E_lib[lib];
+                if (!lib_valid(E, a.L, a.tau, a.Tp)) continue;
+                const int n = a.L - (E - 1) * a.tau - a.Tp;
+                const int RS = table_row_bytes(E + 1);
+                const uint8_t *slot = a.tables + static_cast<size_t>(lib - a.lib0) * a.slot_bytes;
+                for (int c0 = 0; c0 < n; c0 += LK_CR) {
+                    const int s = seq % a.stages, j = seq / a.stages;
+                    if (j > 0) mbar_wait_bounded(&empty[s], (j - 1) & 1, a.flags);
+                    const uint32_t bytes = static_cast<uint32_t>(min(LK_CR, n - c0) * RS);
+                    mbar_arrive_expect_tx(&full[s], bytes);
+                    bulk_copy_g2s(stages + static_cast<size_t>(s) * a.stage_bytes,
+                                  slot + static_cast<size_t>(c0) * RS, bytes, &full[s]);
+                    ++seq;
+                }
+            }
+        }
+        return;
+    }
+
+    // -------------------- consumers
+    const uint8_t *tile = SMEM_TILE ? tile_s : tile_g;
+    if (SMEM_TILE) mbar_wait_bounded(tbar, 0, a.flags);
+    int seq = 0, done = 0;
+    float m[NM];
+    for (int lib = lb0; lib < lb1; ++lib) {
+        const int E = a.E_lib[lib];
+        float *rho_row = a.rho + static_cast<long long>(lib - a.lib0) * a.rho_ld;
+        if (!lib_valid(E, a.L, a.tau, a.Tp)) {
+            if (warp == 0) {
+                for (int j = lane; j < TT; j += 32) {
+                    const int tgt = tile_id * TT + j;
+                    if (tgt < a.N_tgt) rho_row[tgt] = __int_as_float(0x7fc00000);
+                }
+                if (lane == 0 && blockIdx.x == 0) set_flag(a.flags, EDMF_BADARG);
+            }
+            continue;
+        }
+        const int n = a.L - (E - 1) * a.tau - a.Tp, t0 = (E - 1) * a.tau;
+#pragma unroll
+        for (int j = 0; j < NM; ++j) m[j] = 0.f;
+        switch (E + 1) {
+#define EDM_CASE(k) \
+    case k: consume_library<k, BF16, SMEM_TILE>(a, tile, stages, full, empty, seq, n, t0, m); break;
+            EDM_CASE(2) EDM_CASE(3) EDM_CASE(4) EDM_CASE(5) EDM_CASE(6) EDM_CASE(7) EDM_CASE(8)
+            EDM_CASE(9) EDM_CASE(10) EDM_CASE(11) EDM_CASE(12) EDM_CASE(13) EDM_CASE(14)
+            EDM_CASE(15) EDM_CASE(16) EDM_CASE(17) EDM_CASE(18) EDM_CASE(19) EDM_CASE(20)
+            EDM_CASE(21)
+#undef EDM_CASE
+        default: break;
+        }
+        // cross-warp reduction (double-buffered by library parity)
+        float *rb = red + ((done & 1) * LK_NW + warp) * NM * 32;
+#pragma unroll
+        for (int j = 0; j < NM; ++j) rb[j * 32 + lane] = m[j];
+        named_bar_sync(1, LK_NW * 32);
+        if (warp == 0) {
+            const float *base = red + (done & 1) * LK_NW * NM * 32;
+            double S[NM];
+#pragma unroll
+            for (int j = 0; j < NM; ++j) S[j] = 0.0;
+            for (int w = 0; w < LK_NW; ++w)
+#pragma unroll
+                for (int j = 0; j < NM; ++j) S[j] += static_cast<double>(base[(w * NM + j) * 32 + lane]);
+            const double dn = static_cast<double>(n);
+            if (!BF16) {
+                const int tgt = tile_id * 32 + lane;
+                if (tgt < a.N_tgt)
+                    rho_row[tgt] = static_cast<float>(pearson_from_moments(dn, S[0], S[1], S[2], S[3], S[4]));
+            } else {
+                const int tgt = tile_id * 64 + 2 * lane;
+                if (tgt < a.N_tgt)
+                    rho_row[tgt] = static_cast<float>(pearson_from_moments(dn, S[0], S[1], S[2], S[3], S[4]));
+                if (tgt + 1 < a.N_tgt)
+                    rho_row[tgt + 1] =
+                        static_cast<float>(pearson_from_moments(dn, S[5], S[6], S[7], S[8], S[9]));
+            }
+        }
+        ++done;
+    }
+}
+
+edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, const uint8_t *tables,
+                         size_t slot_bytes, const int32_t *E_lib, int lib0, int nlib, int tau,
+                         int Tp, edm_precision prec, float *rho, long long rho_ld) {
+    const bool bf16 = prec == EDM_BF16_TARGETS;
+    const int tt = targets_per_tile(prec);
+    const int n_tiles = (N_tgt + tt - 1) / tt;
+    const int nm = bf16 ? 10 : 5;
+    const size_t tile_bytes = static_cast<size_t>(L) * LK_TILE_ROW;
+    const int stage_bytes = LK_CR * table_row_bytes(EDM_E_MAX + 1);
+    const size_t fixed = static_cast<size_t>(2) * LK_NW * nm * 32 * sizeof(float) +
+                         (2 * LK_MAX_STAGES + 1) * sizeof(uint64_t);
+    const size_t limit = static_cast<size_t>(ctx->max_smem_optin);
+    bool smem_tile = tile_bytes + fixed + 2 * stage_bytes <= limit && tile_bytes < (1u << 20);
+    const size_t avail = limit - fixed - (smem_tile ? tile_bytes : 0);
+    const int stages = static_cast<int>(std::min<size_t>(LK_MAX_STAGES, avail / stage_bytes));
+    if (stages < 2) return set_error(ctx, EDM_ERR_INTERNAL, "lookup: no room for table stages");
+    const size_t smem = (smem_tile ? tile_bytes : 0) + static_cast<size_t>(stages) * stage_bytes +
+                        static_cast<size_t>(2) * LK_NW * nm * 32 * sizeof(float) +
+                        (2 * stages + 1) * sizeof(uint64_t);
+
+    // libraries per CTA: enough CTAs for balance, enough libraries per CTA to
+    // amortise the tile load
+    const long long pairs = static_cast<long long>(nlib) * n_tiles;
+    long long lb = pairs / (8LL * ctx->num_sms);
+    lb = std::max<long long>(1, std::min<long long>(128, lb));
+    LookupArgs a;
+    a.Yt = Yt;
+    a.tables = tables;
+    a.slot_bytes = slot_bytes;
+    a.E_lib = E_lib;
+    a.lib0 = lib0;
+    a.nlib = nlib;
+    a.LB = static_cast<int>(lb);
+    a.L = L;
+    a.tau = tau;
+    a.Tp = Tp;
+    a.N_tgt = N_tgt;
+    a.stages = stages;
+    a.stage_bytes = stage_bytes;
+    a.rho = rho;
+    a.rho_ld = rho_ld;
+    a.flags = ctx->d_flags;
+    dim3 grid(n_tiles, static_cast<unsigned>((nlib + lb - 1) / lb));
+    void (*kern)(const LookupArgs);
+    if (bf16)
+        kern = smem_tile ? lookup_kernel<true, true> : lookup_kernel<true, false>;
+    else
+        kern = smem_tile ? lookup_kernel<false, true> : lookup_kernel<false, false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    before_launch(ctx);
+    kern<<<grid, LK_THREADS, smem, ctx->stream>>>(a);
+    return after_launch(ctx, "lookup_kernel");
+}
+
+}  // namespace edm

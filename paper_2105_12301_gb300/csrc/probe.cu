@@ -1,0 +1,75 @@
+// probe.cu -- measured shared-memory gather bandwidth (the lookup roofline).
+//
+// Each warp reads whole 128-byte rows of a 32 KB shared-memory tile (lane l
+// reads word l of the row), visiting rows in a scattered order fixed at
+// compile time, and folds the values into four independent FP32 sums.  Every
+// read is one conflict-free wavefront and needs one add, so the loop is
+// limited by the shared-memory pipe, as the lookup's gathers are.
+#include "edm_internal.cuh"
+
+namespace edm {
+
+constexpr int PR_ROWS = 256;       // 32 KB tile
+constexpr int PR_WARPS = 16;
+constexpr int PR_UNROLL = 64;
+
+__global__ void __launch_bounds__(PR_WARPS * 32) smem_probe_kernel(int iters, float *sink) {
+    __shared__ __align__(128) float tile[PR_ROWS * 32];
+    for (int i = threadIdx.x; i < PR_ROWS * 32; i += blockDim.x) tile[i] = static_cast<float>(i & 7);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const float *tl = tile + lane;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int base = (threadIdx.x >> 5) * 37;
+    for (int it = 0; it < iters; ++it) {
+        // base row <= 127 and offset <= 127: every row read is < PR_ROWS
+        const float *p = tl + ((base & (PR_ROWS / 2 - 1)) << 5);
+        // scattered compile-time row offsets (149 j) mod 128
+#pragma unroll
+        for (int j = 0; j < PR_UNROLL; j += 4) {
+            a0 += p[((149 * (j + 0)) & (PR_ROWS / 2 - 1)) << 5];
+            a1 += p[((149 * (j + 1)) & (PR_ROWS / 2 - 1)) << 5];
+            a2 += p[((149 * (j + 2)) & (PR_ROWS / 2 - 1)) << 5];
+            a3 += p[((149 * (j + 3)) & (PR_ROWS / 2 - 1)) << 5];
+        }
+        base += 97;
+        base &= (PR_ROWS / 2 - 1);
+    }
+    const float s = a0 + a1 + a2 + a3;
+    if (s == -1.f) sink[blockIdx.x] = s;  // never true; keeps the loads alive
+}
+
+edm_status launch_smem_probe(edm_ctx *ctx, double ms, double *bytes_per_s) {
+    float *sink = nullptr;
+    edm_status st = cuda_check(ctx, cudaMalloc(&sink, sizeof(float) * 4 * ctx->num_sms), "probe");
+    if (st != EDM_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks = 4 * ctx->num_sms;  // 4 CTAs x 16 warps per SM
+    int iters = 64;
+    double got = 0.0;
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        cudaEventRecord(e0, ctx->stream);
+        before_launch(ctx);
+        smem_probe_kernel<<<blocks, PR_WARPS * 32, 0, ctx->stream>>>(iters, sink);
+        st = after_launch(ctx, "smem_probe_kernel");
+        if (st != EDM_OK) break;
+        cudaEventRecord(e1, ctx->stream);
+        st = cuda_check(ctx, cudaEventSynchronize(e1), "probe sync");
+        if (st != EDM_OK) break;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        const double bytes = static_cast<double>(blocks) * PR_WARPS * iters * PR_UNROLL * 128.0;
+        got = bytes / (t * 1e-3);
+        if (t >= 0.5 * ms) break;
+        iters = static_cast<int>(std::min<double>(1 << 24, iters * std::max(2.0, ms / std::max(t, 0.01f))));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    *bytes_per_s = got;
+    return st;
+}
+
+}  // namespace edm

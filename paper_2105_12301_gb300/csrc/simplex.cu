@@ -1,0 +1,178 @@
+// simplex.cu -- optimal embedding dimension by simplex projection.
+//
+// kEDM section 3.3 groups targets by their "optimal embedding dimension"
+// without saying how it is found; the method used here is leave-one-out
+// simplex projection of each series onto itself (section 2.1 steps 1-4 with
+// Y = X and horizon Tp_sel), E = 1..E_max, E* = argmax rho_E.
+//
+// One CTA owns one series (staged in shared memory) and a block of query
+// times; one warp per query time runs knn_row in KNN_SET mode (exact FP64
+// neighbour sets, FP32 distances unless the band had to be resolved), then
+// the weighted prediction.  Prediction and observation are centred on the
+// series mean before their moments are accumulated (FP32 per warp, FP64
+// across warps and CTAs); rho is finished in FP64 by a second kernel.
+#include "knn_core.cuh"
+
+namespace edm {
+
+constexpr int SX_WARPS = 8;
+constexpr int SX_SERIES_SMEM_MAX = 96 * 1024;
+
+template <int E>
+__device__ __forceinline__ void simplex_row(const float *xs, int t, int lo, int hi, int tau, int Tp,
+                                            float mu, WarpScratch *ws, float (&m)[5]) {
+    constexpr int K = E + 1;
+    const int lane = lane_id();
+    int u = 0;
+    float d = 0.f;
+    knn_row<E, KNN_SET>(xs, t, lo, hi, tau, K, ws, &u, &d);
+    const float w = simplex_weight(d, K);
+    const float part = lane < K ? w * __fsub_rn(xs[u + Tp], mu) : 0.f;
+    const float a = warp_sum(part);
+    const float b = __fsub_rn(xs[t + Tp], mu);
+    if (lane == E - 1) {
+        m[0] += a;
+        m[1] += b;
+        m[2] = __fmaf_rn(a, a, m[2]);
+        m[3] = __fmaf_rn(b, b, m[3]);
+        m[4] = __fmaf_rn(a, b, m[4]);
+    }
+}
+
+// partial [N][nrb][E_max][5] FP64 moments of (prediction, observation).
+template <bool SMEM>
+__global__ void __launch_bounds__(SX_WARPS * 32)
+    simplex_kernel(const float *__restrict__ X, int L, int E_max, int tau, int Tp, int TB, int nrb,
+                   double *__restrict__ partial) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    WarpScratch *wsa = reinterpret_cast<WarpScratch *>(smem);
+    float *red = reinterpret_cast<float *>(smem + SX_WARPS * sizeof(WarpScratch));  // [W][32][5]
+    double *mu_s = reinterpret_cast<double *>(red + SX_WARPS * 32 * 5);               // [W]
+    float *xs_s = reinterpret_cast<float *>(mu_s + SX_WARPS);
+    const int series = blockIdx.x, rb = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const float *xg = X + static_cast<size_t>(series) * L;
+
+    // series mean in FP64, fixed reduction order (same in every CTA)
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) acc += static_cast<double>(xg[i]);
+    acc = warp_sum_d(acc);
+    if (lane == 0) mu_s[warp] = acc;
+    const float *xs = xg;
+    if (SMEM) {
+        for (int i = threadIdx.x; i < L; i += blockDim.x) xs_s[i] = xg[i];
+        xs = xs_s;
+    }
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < SX_WARPS; ++w) tot += mu_s[w];
+    const float mu = static_cast<float>(tot / L);
+
+    float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // lane e: moments of E = e+1
+    WarpScratch *ws = wsa + warp;
+    const int t_begin = rb * TB, t_end = t_begin + TB;  // this CTA's query times
+    for (int E = 1; E <= E_max; ++E) {
+        const int lo = (E - 1) * tau, hi = L - 1 - Tp;
+        if (hi - lo + 1 < E + 2) break;  // too few points for this and larger E
+        const int a0 = max(lo, t_begin), a1 = min(hi + 1, t_end);
+        for (int t = a0 + warp; t < a1; t += SX_WARPS) {
+            switch (E) {
+#define EDM_CASE(e) \
+    case e: simplex_row<e>(xs, t, lo, hi, tau, Tp, mu, ws, m); break;
+                EDM_CASE(1) EDM_CASE(2) EDM_CASE(3) EDM_CASE(4) EDM_CASE(5) EDM_CASE(6)
+                EDM_CASE(7) EDM_CASE(8) EDM_CASE(9) EDM_CASE(10) EDM_CASE(11) EDM_CASE(12)
+                EDM_CASE(13) EDM_CASE(14) EDM_CASE(15) EDM_CASE(16) EDM_CASE(17) EDM_CASE(18)
+                EDM_CASE(19) EDM_CASE(20)
+#undef EDM_CASE
+            default: break;
+            }
+        }
+    }
+    // cross-warp reduction in FP64, fixed order
+#pragma unroll
+    for (int j = 0; j < 5; ++j) red[(warp * 32 + lane) * 5 + j] = m[j];
+    __syncthreads();
+    for (int i = threadIdx.x; i < E_max * 5; i += blockDim.x) {
+        const int e = i / 5, j = i % 5;
+        double s = 0.0;
+        for (int w = 0; w < SX_WARPS; ++w) s += static_cast<double>(red[(w * 32 + e) * 5 + j]);
+        partial[((static_cast<size_t>(series) * nrb + rb) * E_max + e) * 5 + j] = s;
+    }
+}
+
+// One thread per series: sum the partials, rho per E, argmax.
+__global__ void simplex_finish_kernel(const double *__restrict__ partial, int N, int L, int E_max,
+                                      int tau, int Tp, int nrb, int32_t *__restrict__ E_opt,
+                                      float *__restrict__ rho_E) {
+    const int series = blockIdx.x * blockDim.x + threadIdx.x;
+    if (series >= N) return;
+    int best_E = 1;
+    double best = 0.0;
+    bool have = false;
+    for (int E = 1; E <= E_max; ++E) {
+        const int n = L - (E - 1) * tau - Tp;
+        double r = __longlong_as_double(0x7ff8000000000000LL);
+        if (n >= E + 2) {
+            double S[5] = {0, 0, 0, 0, 0};
+            for (int rb = 0; rb < nrb; ++rb)
+                for (int j = 0; j < 5; ++j)
+                    S[j] += partial[((static_cast<size_t>(series) * nrb + rb) * E_max + (E - 1)) * 5 + j];
+            r = pearson_from_moments(static_cast<double>(n), S[0], S[1], S[2], S[3], S[4]);
+        }
+        if (rho_E) rho_E[static_cast<size_t>(series) * E_max + (E - 1)] = static_cast<float>(r);
+        if (!isnan(r) && (!have || r > best)) {
+            best = r;
+            best_E = E;
+            have = true;
+        }
+    }
+    E_opt[series] = best_E;
+}
+
+static void simplex_geometry(edm_ctx *ctx, int N, int L, int &TB, int &nrb) {
+    const long long want_ctas = 8LL * ctx->num_sms;
+    long long per_series = (want_ctas + N - 1) / N;
+    TB = static_cast<int>((L + per_series - 1) / per_series);
+    TB = std::max(TB, 4 * SX_WARPS);
+    TB = std::min(TB, L);
+    nrb = (L + TB - 1) / TB;
+}
+
+size_t simplex_workspace_bytes(edm_ctx *ctx, int N, int L, int E_max) {
+    int TB, nrb;
+    simplex_geometry(ctx, N, L, TB, nrb);
+    return sizeof(double) * static_cast<size_t>(N) * nrb * E_max * 5;
+}
+
+edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max, int tau,
+                          int Tp_sel, int32_t *E_opt, float *rho_E) {
+    int TB, nrb;
+    simplex_geometry(ctx, N, L, TB, nrb);
+    edm_status st = ws_reserve(ctx, simplex_workspace_bytes(ctx, N, L, E_max));
+    if (st != EDM_OK) return st;
+    double *partial = static_cast<double *>(ctx->ws);
+    const bool smem_series = sizeof(float) * static_cast<size_t>(L) <= SX_SERIES_SMEM_MAX;
+    const size_t smem = SX_WARPS * sizeof(WarpScratch) + SX_WARPS * 32 * 5 * sizeof(float) +
+                        SX_WARPS * sizeof(double) +
+                        (smem_series ? align_up(sizeof(float) * L, 16) : 0);
+    dim3 grid(N, nrb);
+    if (smem_series) {
+        auto kern = simplex_kernel<true>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        before_launch(ctx);
+        kern<<<grid, SX_WARPS * 32, smem, ctx->stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial);
+    } else {
+        auto kern = simplex_kernel<false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        before_launch(ctx);
+        kern<<<grid, SX_WARPS * 32, smem, ctx->stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial);
+    }
+    st = after_launch(ctx, "simplex_kernel");
+    if (st != EDM_OK) return st;
+    before_launch(ctx);
+    simplex_finish_kernel<<<(N + 127) / 128, 128, 0, ctx->stream>>>(partial, N, L, E_max, tau,
+                                                                      Tp_sel, nrb, E_opt, rho_E);
+    return after_launch(ctx, "simplex_finish_kernel");
+}
+
+}  // namespace edm

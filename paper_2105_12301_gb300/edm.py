@@ -1,0 +1,218 @@
+"""ctypes binding of libedm (include/edm.h), same names as the C ABI.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of libedm.so.  Tensors must be CUDA tensors (float32 series, int32
+E arrays), C-contiguous; results are allocated as CUDA tensors on the same
+device.  Calls are enqueued on torch's current stream of that device.
+
+There is no CPU path: if libedm.so is missing or no GPU is present, the
+calls raise.
+"""
+import ctypes
+import os
+import threading
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libedm.so")
+
+EDM_OK = 0
+EDM_FP32 = 0
+EDM_BF16_TARGETS = 1
+EDM_E_MAX = 20
+EDM_K_MAX = 24
+EDM_L_MAX = 65535
+
+_STATUS = {0: "EDM_OK", 1: "EDM_ERR_INVALID_ARG", 2: "EDM_ERR_CUDA", 3: "EDM_ERR_OOM",
+           4: "EDM_ERR_TIMEOUT", 5: "EDM_ERR_INTERNAL"}
+
+
+class EdmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (_STATUS.get(status, str(status)), message))
+        self.status = status
+
+
+class edm_instance(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("N", ctypes.c_int), ("L", ctypes.c_int),
+                ("E_lib", ctypes.c_void_p), ("tau", ctypes.c_int), ("Tp", ctypes.c_int),
+                ("rho", ctypes.c_void_p), ("lib_begin", ctypes.c_int),
+                ("lib_end", ctypes.c_int)]
+
+
+_lib = None
+_lock = threading.Lock()
+_ctxs = {}
+
+
+def load():
+    """Load libedm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libedm.so not found at %s: run "
+                           "`python -m paper_2105_12301_gb300.build`" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, ci = ctypes.c_void_p, ctypes.c_int
+    lib.edm_create.argtypes = [ctypes.POINTER(vp), ci, vp]
+    lib.edm_destroy.argtypes = [vp]
+    lib.edm_set_stream.argtypes = [vp, vp]
+    lib.edm_ctx_sync.argtypes = [vp]
+    lib.edm_status_string.argtypes = [ci]
+    lib.edm_status_string.restype = ctypes.c_char_p
+    lib.edm_last_error.argtypes = [vp]
+    lib.edm_last_error.restype = ctypes.c_char_p
+    lib.edm_kernel_launches.argtypes = [vp]
+    lib.edm_kernel_launches.restype = ctypes.c_uint64
+    lib.edm_embed.argtypes = [vp, vp, ci, ci, ci, vp]
+    lib.edm_knn.argtypes = [vp, vp, ci, ci, ci, ci, ci, ci, vp, vp]
+    lib.edm_simplex_optimal_E.argtypes = [vp, vp, ci, ci, ci, ci, ci, vp, vp]
+    lib.edm_ccm_all.argtypes = [vp, vp, ci, vp, ci, ci, vp, ci, ci, ci, vp]
+    lib.edm_ccm_batched.argtypes = [vp, ctypes.POINTER(edm_instance), ci, ci]
+    for f in ("edm_create", "edm_destroy", "edm_set_stream", "edm_ctx_sync", "edm_embed",
+              "edm_knn", "edm_simplex_optimal_E", "edm_ccm_all", "edm_ccm_batched"):
+        getattr(lib, f).restype = ci
+    _lib = lib
+    return lib
+
+
+def _ctx(device):
+    """The context of a CUDA device, bound to torch's current stream."""
+    lib = load()
+    dev = torch.device(device)
+    idx = dev.index if dev.index is not None else torch.cuda.current_device()
+    with _lock:
+        ctx = _ctxs.get(idx)
+        if ctx is None:
+            p = ctypes.c_void_p()
+            st = lib.edm_create(ctypes.byref(p), idx, None)
+            if st != EDM_OK:
+                raise EdmError(st, "edm_create(device=%d) failed" % idx)
+            ctx = p
+            _ctxs[idx] = ctx
+    stream = torch.cuda.current_stream(idx).cuda_stream
+    lib.edm_set_stream(ctx, ctypes.c_void_p(stream))
+    return ctx
+
+
+def _check(ctx, st, what):
+    if st != EDM_OK:
+        msg = load().edm_last_error(ctx).decode() if ctx else ""
+        raise EdmError(st, "%s: %s" % (what, msg))
+
+
+def _series(x, name, ndim):
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if x.dtype != torch.float32 or x.dim() != ndim or not x.is_contiguous():
+        raise TypeError("%s must be a contiguous float32 tensor with %d dims" % (name, ndim))
+    return x
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def edm_ctx_sync(device=None):
+    """Wait for the device and raise the first device-side error since the
+    previous sync (out-of-range E on the device, a timed-out wait)."""
+    dev = device if device is not None else torch.cuda.current_device()
+    ctx = _ctx(dev)
+    _check(ctx, load().edm_ctx_sync(ctx), "edm_ctx_sync")
+
+
+def edm_kernel_launches(device=None):
+    dev = device if device is not None else torch.cuda.current_device()
+    return int(load().edm_kernel_launches(_ctx(dev)))
+
+
+def edm_embed(x, E, tau=1):
+    """Delay embedding of one series x [L] -> [L-(E-1)tau][E] float32."""
+    _series(x, "x", 1)
+    L = x.shape[0]
+    out = torch.empty((max(L - (E - 1) * tau, 0), E), dtype=torch.float32, device=x.device)
+    ctx = _ctx(x.device)
+    _check(ctx, load().edm_embed(ctx, _ptr(x), L, E, tau, _ptr(out)), "edm_embed")
+    return out
+
+
+def edm_knn(X, E, tau=1, Tp=0, k=None, with_dist=True):
+    """All-kNN of every series of X [N][L]: (idx [N][n][k] int32 time
+    indices, dist [N][n][k] float32 or None)."""
+    _series(X, "X", 2)
+    N, L = X.shape
+    k = E + 1 if k is None else k
+    n = L - (E - 1) * tau - Tp
+    idx = torch.empty((N, max(n, 0), k), dtype=torch.int32, device=X.device)
+    dist = torch.empty((N, max(n, 0), k), dtype=torch.float32, device=X.device) if with_dist else None
+    ctx = _ctx(X.device)
+    _check(ctx, load().edm_knn(ctx, _ptr(X), N, L, E, tau, Tp, k, _ptr(idx), _ptr(dist)),
+           "edm_knn")
+    return idx, dist
+
+
+def edm_simplex_optimal_E(X, E_max=EDM_E_MAX, tau=1, Tp_sel=1, with_rho=True):
+    """(E_opt [N] int32, rho_E [N][E_max] float32 or None) for X [N][L]."""
+    _series(X, "X", 2)
+    N, L = X.shape
+    E_opt = torch.empty(N, dtype=torch.int32, device=X.device)
+    rho_E = torch.empty((N, E_max), dtype=torch.float32, device=X.device) if with_rho else None
+    ctx = _ctx(X.device)
+    _check(ctx, load().edm_simplex_optimal_E(ctx, _ptr(X), N, L, E_max, tau, Tp_sel,
+                                             _ptr(E_opt), _ptr(rho_E)), "edm_simplex_optimal_E")
+    return E_opt, rho_E
+
+
+def _prec(precision):
+    if precision in ("fp32", EDM_FP32):
+        return EDM_FP32
+    if precision in ("bf16", EDM_BF16_TARGETS):
+        return EDM_BF16_TARGETS
+    raise ValueError("precision must be 'fp32' or 'bf16'")
+
+
+def edm_ccm_all(X_lib, Y_tgt, E_lib, tau=1, Tp=0, precision="fp32", out=None):
+    """rho [N_lib][N_tgt]: skill of library i's manifold at predicting target j."""
+    _series(X_lib, "X_lib", 2)
+    _series(Y_tgt, "Y_tgt", 2)
+    if X_lib.shape[1] != Y_tgt.shape[1]:
+        raise ValueError("libraries and targets must have the same length")
+    if E_lib.dtype != torch.int32 or not E_lib.is_cuda or E_lib.shape != (X_lib.shape[0],):
+        raise TypeError("E_lib must be a CUDA int32 tensor of shape [N_lib]")
+    E_lib = E_lib.contiguous()
+    N_lib, L = X_lib.shape
+    N_tgt = Y_tgt.shape[0]
+    rho = out if out is not None else torch.empty((N_lib, N_tgt), dtype=torch.float32,
+                                                  device=X_lib.device)
+    if rho.shape != (N_lib, N_tgt) or rho.dtype != torch.float32 or not rho.is_contiguous():
+        raise TypeError("out must be a contiguous float32 [N_lib][N_tgt] tensor")
+    ctx = _ctx(X_lib.device)
+    _check(ctx, load().edm_ccm_all(ctx, _ptr(X_lib), N_lib, _ptr(Y_tgt), N_tgt, L, _ptr(E_lib),
+                                   tau, Tp, _prec(precision), _ptr(rho)), "edm_ccm_all")
+    return rho
+
+
+def edm_ccm_batched(problems, precision="fp32"):
+    """problems: list of dicts with X [N][L], E_lib [N] int32, tau, Tp and
+    optional lib_begin/lib_end; returns the list of rho blocks."""
+    arr = (edm_instance * len(problems))()
+    outs = []
+    device = None
+    for i, p in enumerate(problems):
+        X = _series(p["X"], "X", 2)
+        N, L = X.shape
+        b, e = p.get("lib_begin", 0), p.get("lib_end", N)
+        rho = torch.empty((e - b, N), dtype=torch.float32, device=X.device)
+        E_lib = p["E_lib"].contiguous()
+        outs.append((rho, X, E_lib))
+        arr[i] = edm_instance(X.data_ptr(), N, L, E_lib.data_ptr(), p.get("tau", 1),
+                              p.get("Tp", 0), rho.data_ptr(), b, e)
+        device = X.device
+    if not problems:
+        return []
+    ctx = _ctx(device)
+    _check(ctx, load().edm_ccm_batched(ctx, arr, len(problems), _prec(precision)),
+           "edm_ccm_batched")
+    return [o[0] for o in outs]

@@ -1,0 +1,159 @@
+"""GPU parity of optimal-E selection and all-to-all CCM against the FP64 oracle.
+
+Tolerances: |rho_gpu - rho_oracle| <= 1e-5 with FP32 target storage and
+<= 1e-3 with BF16 target storage; the skills rho_E of the simplex sweep
+within 1e-5; E* equal to the oracle's unless the oracle's own skills of the
+two choices lie within 1e-5 of each other (a near-tie).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2105_12301_gb300 import edm, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-5
+TOL_BF16 = 1e-3
+TOL_RHO_E = 1e-5
+
+
+def gpu(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def check_optimal_E(X, E_max, tau=1, Tp_sel=1):
+    E_gpu, rho_gpu = edm.edm_simplex_optimal_E(gpu(X), E_max, tau, Tp_sel)
+    edm.edm_ctx_sync()
+    E_gpu, rho_gpu = E_gpu.cpu().numpy(), rho_gpu.cpu().numpy()
+    E_or, rho_or = oracle.optimal_E_many(X, E_max, tau, Tp_sel)
+    np.testing.assert_array_equal(np.isnan(rho_gpu), np.isnan(rho_or))
+    ok = ~np.isnan(rho_or)
+    assert np.max(np.abs(rho_gpu[ok] - rho_or[ok]), initial=0.0) <= TOL_RHO_E
+    for i in np.nonzero(E_gpu != E_or)[0]:
+        gap = abs(rho_or[i, E_gpu[i] - 1] - rho_or[i, E_or[i] - 1])
+        assert gap <= 1e-5, (i, E_gpu[i], E_or[i], gap)
+    return E_gpu
+
+
+def check_ccm(X_lib, Y, E_lib, tau, Tp, precision, tol, lib_rows=None):
+    rho = edm.edm_ccm_all(gpu(X_lib), gpu(Y), gpu(E_lib.astype(np.int32)), tau, Tp, precision)
+    edm.edm_ctx_sync()
+    rho = rho.cpu().numpy()
+    rows = np.arange(X_lib.shape[0]) if lib_rows is None else np.asarray(lib_rows)
+    ref = oracle.ccm_matrix(X_lib, Y, E_lib, tau, Tp, lib_rows=rows)
+    got = rho[rows]
+    np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    err = np.max(np.abs(got[ok] - ref[ok]), initial=0.0)
+    assert err <= tol, err
+    return rho, err
+
+
+def test_config1_optimal_E_and_full_rho_matrix():
+    X = inputs.config1()
+    E = check_optimal_E(X, 10)
+    check_ccm(X, X, E, 1, 0, "fp32", TOL_FP32)
+    check_ccm(X, X, E, 1, 0, "bf16", TOL_BF16)
+
+
+def test_config2_sampled_libraries():
+    X = inputs.config2()
+    rows = np.arange(0, 1000, 71)
+    E = check_optimal_E(X[rows], 20)
+    E_all = np.full(1000, 3, np.int32)
+    E_all[rows] = E
+    check_ccm(X, X, E_all, 1, 0, "fp32", TOL_FP32, lib_rows=rows)
+    check_ccm(X, X, E_all, 1, 0, "bf16", TOL_BF16, lib_rows=rows)
+
+
+@pytest.mark.parametrize("E", [1, 2, 7, 20])
+def test_every_K_specialisation(E):
+    X = inputs.coupled_logistic(5, 180, 100 + E)
+    E_lib = np.full(5, E, np.int32)
+    check_ccm(X, X, E_lib, 1, 0, "fp32", TOL_FP32)
+
+
+def test_ragged_counts_tau_and_horizon():
+    X = inputs.coupled_logistic(3, 90, 8)
+    Y = inputs.coupled_logistic(70, 90, 9)        # 70 targets: ragged tiles
+    E_lib = np.array([2, 5, 3], np.int32)
+    check_ccm(X, Y, E_lib, 3, 2, "fp32", TOL_FP32)
+    check_ccm(X, Y, E_lib, 3, 2, "bf16", TOL_BF16)
+
+
+def test_mixed_E_in_one_launch():
+    X = inputs.config2(N=40, L=400)
+    E_lib = np.arange(40, dtype=np.int32) % 20 + 1
+    check_ccm(X, X, E_lib, 1, 0, "fp32", TOL_FP32)
+
+
+def test_long_series_gathers_from_global_memory():
+    # L = 2500: a 32-target FP32 tile no longer fits shared memory
+    X = inputs.coupled_logistic(40, 2500, 12)
+    E_lib = np.array([1, 2, 3, 4] * 10, np.int32)
+    check_ccm(X, X, E_lib, 1, 0, "fp32", TOL_FP32, lib_rows=[0, 13, 39])
+    check_ccm(X, X, E_lib, 1, 0, "bf16", TOL_BF16, lib_rows=[0, 13, 39])
+
+
+def test_self_map_equals_simplex():
+    X = inputs.config1()
+    E_gpu, rho_E = edm.edm_simplex_optimal_E(gpu(X), 6, 1, 0)
+    rho = edm.edm_ccm_all(gpu(X), gpu(X), E_gpu, 1, 0).cpu().numpy()
+    rho_E = rho_E.cpu().numpy()
+    E_np = E_gpu.cpu().numpy()
+    for i in range(16):
+        assert abs(rho[i, i] - rho_E[i, E_np[i] - 1]) <= 2e-6
+
+
+def test_constant_target_and_bad_E_give_nan():
+    X = inputs.coupled_logistic(2, 100, 3)
+    Y = np.vstack([X, np.full((1, 100), 1.5, np.float32)])
+    rho = edm.edm_ccm_all(gpu(X), gpu(Y), gpu(np.array([2, 2], np.int32))).cpu().numpy()
+    assert np.all(np.isnan(rho[:, 2])) and np.all(np.isfinite(rho[:, :2]))
+    rho = edm.edm_ccm_all(gpu(X), gpu(Y), gpu(np.array([2, 33], np.int32)))
+    with pytest.raises(edm.EdmError):
+        edm.edm_ctx_sync()
+    rho = rho.cpu().numpy()
+    assert np.all(np.isnan(rho[1])) and np.all(np.isfinite(rho[0, :2]))
+
+
+def test_batched_instances_match_single_calls():
+    probs = []
+    for i, (N, L) in enumerate([(33, 250), (70, 130), (5, 600)]):
+        X = inputs.coupled_logistic(N, L, 200 + i)
+        E = (np.arange(N) % 4 + 1).astype(np.int32)
+        probs.append({"X": gpu(X), "E_lib": gpu(E), "tau": 1, "Tp": 0,
+                      "lib_begin": 1, "lib_end": N})
+    outs = edm.edm_ccm_batched(probs)
+    for p, out in zip(probs, outs):
+        ref = edm.edm_ccm_all(p["X"][1:].contiguous(), p["X"], p["E_lib"][1:].contiguous())
+        torch.testing.assert_close(out, ref, rtol=0, atol=0, equal_nan=True)
+    edm.edm_ctx_sync()
+
+
+def test_full_size_calcium_workload_sampled():
+    # 50,000 x 1,500 as timed by the bench: GPU runs everything, the oracle
+    # checks sampled libraries against all 50,000 targets
+    X = inputs.config3()
+    Xg = gpu(X)
+    E_gpu, rho_E = edm.edm_simplex_optimal_E(Xg, 20, 1, 1)
+    rows = [0, 17, 31337, 49999]
+    E_np = E_gpu.cpu().numpy()
+    E_or, rho_or = oracle.optimal_E_many(X[rows], 20, 1, 1)
+    got = rho_E.cpu().numpy()[rows]
+    assert np.max(np.abs(got - rho_or)) <= TOL_RHO_E
+    for r, e in zip(rows, E_or):
+        if E_np[r] != e:
+            assert abs(rho_or[rows.index(r), E_np[r] - 1] - rho_or[rows.index(r), e - 1]) <= 1e-5
+    rho = edm.edm_ccm_all(Xg, Xg, E_gpu, 1, 0, "fp32")
+    edm.edm_ctx_sync()
+    ref = oracle.ccm_matrix(X, X, E_np, 1, 0, lib_rows=rows)
+    err = np.max(np.abs(rho[rows].cpu().numpy() - ref))
+    assert err <= TOL_FP32, err
+    del rho
+    rho = edm.edm_ccm_all(Xg, Xg, E_gpu, 1, 0, "bf16")
+    edm.edm_ctx_sync()
+    err = np.max(np.abs(rho[rows].cpu().numpy() - ref))
+    assert err <= TOL_BF16, err
