@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""Benchmark of all-to-all convergent cross mapping on GB300.
+
+One step is one pass of the whole hot path over the calcium-imaging-shaped
+workload (50,000 series x 1,500 steps, inputs resident in HBM):
+  optimal E of every series (simplex, E = 1..20, Tp_sel = 1)
+  -> exact neighbour tables (k = E*+1) of every library
+  -> lookup + Pearson for all 2.5e9 (library, target) pairs (tau = 1, Tp = 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line.  `value` is CCM pairs/s of the plain FP32 path, timed
+with CUDA events on the launching stream over K steps; the mixed-precision
+form (BF16 target storage) is reported beside it under "mixed".  With N > 1
+(torchrun) every rank runs its own problem of the same shape (weak scaling,
+no data exchange); the step time is the maximum over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+from paper_2105_12301_gb300 import inputs, ranks  # noqa: E402
+
+METRIC = ("CCM pairs/s (lib×target, L=1500) + kNN rows/s; mixed vs plain at "
+          "|Δrho|≤1e-4")
+UNIT = "pairs/s"
+E_MAX, TAU, TP, TP_SEL = 20, 1, 0, 1
+
+# DRAM bytes per lookup_kernel launch from an ncu capture (profiles/), valid
+# only for the kernel source it was taken on.
+LOOKUP_TRAFFIC = {"source_sha1": None, "bytes_per_launch": None}
+
+
+def workload(name):
+    if name == "calcium50k":
+        return 50000, 1500
+    if name == "calcium2k":
+        return 2000, 1500
+    raise ValueError(name)
+
+
+def workload_config(name, N, L, world_size):
+    return {
+        "workload": "calcium-imaging-shaped all-to-all CCM, %d series x %d steps "
+                    "(Lorenz-63 driver + AR(1), exp-filtered, z-normalised)" % (N, L),
+        "n_series": N, "series_len": L, "pairs_per_step": N * N,
+        "E_range": [1, E_MAX], "tau": TAU, "Tp": TP, "Tp_sel": TP_SEL,
+        "libraries": "all series", "targets": "all series",
+        "parallelism": "independent problem per GPU" if world_size > 1 else "single GPU",
+        "l2": "inputs larger than L2 (300 MB series, 10 GB rho, GB-scale tables); no flush",
+    }
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------- CPU baseline
+
+def cpu_sample(X, n_libs, threads):
+    """The FP64 oracle on n_libs libraries x all targets (optimal E included);
+    returns (pairs/s, seconds)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+
+    rows = np.linspace(0, X.shape[0] - 1, n_libs).astype(int)
+
+    def one(i):
+        e, _ = oracle.optimal_E(X[i], E_MAX, TAU, TP_SEL)
+        return oracle.ccm_row(X[i], X, e, TAU, TP)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(one, rows))
+    dt = time.perf_counter() - t0
+    return n_libs * X.shape[0] / dt, dt
+
+
+def run_reference(args):
+    rank, size = ranks.init("gloo")
+    if rank != 0:
+        return
+    N, L = workload(args.workload)
+    X = inputs.config3(N, L)
+    cores = os.cpu_count() or 1
+    threads = cores
+    n_libs = threads
+    for _ in range(args.warmup):
+        cpu_sample(X, max(1, threads // 4), threads)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        v, dt = cpu_sample(X, n_libs, threads)
+        vals.append(v)
+        secs.append(dt)
+    value = float(np.mean(vals))
+    sample = ("%d libraries x all %d targets per step (optimal E over 1..%d + CCM row), "
+              "%d threads" % (n_libs, N, E_MAX, threads))
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.workload, N, L, 1),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------- GPU arm
+
+def source_sha1(path):
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()
+
+
+def run_gb300(args):
+    from paper_2105_12301_gb300 import edm
+
+    rank, size = ranks.init()
+    _, _, local = ranks.world()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N, L = workload(args.workload)
+    X = inputs.config3(N, L, seed=ranks.problem_seed(1003, rank))
+    Xg = torch.from_numpy(X).to(dev)
+    rho = torch.empty((N, N), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(prec):
+        E_opt, _ = edm.edm_simplex_optimal_E(Xg, E_MAX, TAU, TP_SEL, with_rho=False)
+        edm.edm_ccm_all(Xg, Xg, E_opt, TAU, TP, prec, out=rho)
+        return E_opt
+
+    def timed(prec, warmup, steps, profile=False):
+        for _ in range(warmup):
+            step(prec)
+        torch.cuda.synchronize(dev)
+        if profile:
+            edm.edm_profile_enable(True, dev)
+        launches0 = edm.edm_kernel_launches(dev)
+        ranks.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            E_opt = step(prec)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ranks.barrier()
+        ms = e0.elapsed_time(e1) / steps
+        launches = edm.edm_kernel_launches(dev) - launches0
+        edm.edm_ctx_sync(dev)
+        return ms, launches, E_opt
+
+    # roofline denominator: this GPU's shared-memory gather bandwidth
+    smem_peak_gbs = edm.edm_probe_smem_bandwidth(200.0, dev) / 1e9
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, launches, E_opt = timed(args.precision, args.warmup, args.steps, profile=True)
+    clk = clocks.stop()
+    ms_max = ranks.max_over_ranks(ms, dev)
+    pairs = float(N) * N
+    value = size * pairs / (ms_max / 1e3)
+
+    # per-kernel device times of the timed steps
+    prof = {k: edm.edm_profile_read(k, dev) for k in ("sweep_kernel", "simplex_kernel", "simplex_finish_kernel",
+                                      "ccm_table_kernel", "lookup_kernel", "target_store_kernel",
+                                      "target_mean_kernel")}
+    edm.edm_profile_enable(False, dev)
+    E_np = E_opt.cpu().numpy().astype(np.int64)
+    n_lib = L - (E_np - 1) * TAU - TP                       # rows per library table
+    k_lib = E_np + 1
+    bpv = 4 if args.precision == "fp32" else 2
+    # algorithmic shared-memory gather bytes of one step: every (row, neighbour)
+    # and every observation, for every target
+    lookup_bytes = float(np.sum(n_lib * (k_lib + 1))) * N * bpv
+    lk_ms, lk_n = prof["lookup_kernel"]
+    lk_avg_ms = lk_ms / max(lk_n, 1)
+    achieved_gbs = lookup_bytes * args.steps / (lk_ms / 1e3) / 1e9 if lk_ms > 0 else None
+    sweep_rows = sum(max(0, L - (e - 1) * TAU - TP_SEL) for e in range(1, E_MAX + 1)
+                     if L - (e - 1) * TAU - TP_SEL >= e + 2) * N
+    table_rows = float(np.sum(n_lib))
+    knn_ms = (prof["sweep_kernel"][0] + prof["simplex_kernel"][0] +
+              prof["ccm_table_kernel"][0]) / args.steps
+    knn_rows_per_s = (sweep_rows + table_rows) / (knn_ms / 1e3) if knn_ms > 0 else None
+    lookup_src = os.path.join(ROOT, "paper_2105_12301_gb300", "csrc", "lookup.cu")
+    traffic = (LOOKUP_TRAFFIC["bytes_per_launch"]
+               if LOOKUP_TRAFFIC["source_sha1"] == source_sha1(lookup_src) else None)
+    roofline = {
+        "bound": "smem", "kernel": "lookup_kernel",
+        "achieved": achieved_gbs, "peak": smem_peak_gbs, "unit": "GB/s",
+        "frac": (achieved_gbs / smem_peak_gbs) if achieved_gbs and smem_peak_gbs else None,
+        "traffic": traffic,
+        "peak_source": "measured: edm_probe_smem_bandwidth (conflict-free 128-B row gathers, "
+                       "all SMs, this run)",
+        "algorithmic_bytes_per_launch": lookup_bytes * args.steps / max(lk_n, 1),
+        "avg_launch_ms": lk_avg_ms,
+        "nominal_peak_at_sampled_clock_gbs": (152 * 128 * clk["sm_mhz"] * 1e6 / 1e9) if clk else None,
+    }
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": size,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f32+bf16-targets",
+        "data": "synthetic",
+        "config": workload_config(args.workload, N, L, size),
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "knn_rows_per_s": knn_rows_per_s,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+        "roofline": roofline,
+        "E_opt_hist": np.bincount(E_np, minlength=E_MAX + 1)[1:].tolist(),
+    }
+
+    if args.mixed and args.precision == "fp32":
+        ms_m, _, _ = timed("bf16", 1, max(1, args.steps - 1))
+        ms_m = ranks.max_over_ranks(ms_m, dev)
+        out["mixed"] = {"value": size * pairs / (ms_m / 1e3), "unit": UNIT, "ms_per_step": ms_m,
+                        "dtype": "f32+bf16-targets", "tolerance": "|drho| <= 1e-3 (tests)"}
+
+    if args.e2e:
+        # public API end to end: pinned host series in, rho out, every step
+        X_h = torch.from_numpy(X).pin_memory()
+        rho_h = torch.empty((N, N), dtype=torch.float32, pin_memory=True)
+        steps_e2e = max(1, min(args.steps, 2))
+
+        def e2e_step():
+            Xg.copy_(X_h, non_blocking=True)
+            step(args.precision)
+            rho_h.copy_(rho, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        ranks.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps_e2e):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_e = ranks.max_over_ranks(e0.elapsed_time(e1) / steps_e2e, dev)
+        out["e2e"] = {"value": size * pairs / (ms_e / 1e3), "unit": UNIT,
+                      "h2d_bytes_per_step": int(X_h.numel() * 4),
+                      "d2h_bytes_per_step": int(rho_h.numel() * 4), "ms_per_step": ms_e,
+                      "steps": steps_e2e}
+        del rho_h
+
+    if args.cpu_baseline and rank == 0 and size == 1:
+        cores = os.cpu_count() or 1
+        v, dt = cpu_sample(X, cores * 3, cores)
+        out["cpu_baseline"] = {
+            "value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d libraries x all %d targets (optimal E over 1..%d + CCM row), %.1f s"
+                      % (cores * 3, N, E_MAX, dt)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", choices=["calcium50k", "calcium2k"], default="calcium50k")
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--no-mixed", dest="mixed", action="store_false")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

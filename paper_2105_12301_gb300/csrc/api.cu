@@ -104,24 +104,27 @@ static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, int N_lib, const flo
                           edm_precision prec, float *rho) {
     const size_t yt_bytes = target_store_bytes(N_tgt, L, prec);
     const size_t mean_bytes = align_up(sizeof(double) * N_tgt, 256);
+    const size_t sums_bytes = align_up(sizeof(double) * N_tgt * EDM_E_MAX, 256);
     const size_t slot = ccm_slot_bytes(L, tau, Tp);
     if (slot == 0) return set_error(ctx, EDM_ERR_INVALID_ARG, "series too short");
     const int chunk = static_cast<int>(
         std::max<size_t>(1, std::min<size_t>(N_lib, ctx->table_budget / slot)));
-    edm_status st = ws_reserve(ctx, yt_bytes + mean_bytes + chunk * slot);
+    edm_status st = ws_reserve(ctx, yt_bytes + mean_bytes + 2 * sums_bytes + chunk * slot);
     if (st != EDM_OK) return st;
     uint8_t *base = static_cast<uint8_t *>(ctx->ws);
     uint8_t *Yt = base;
     double *mean = reinterpret_cast<double *>(base + yt_bytes);
-    uint8_t *tables = base + yt_bytes + mean_bytes;
-    st = launch_target_store(ctx, Y_tgt, N_tgt, L, prec, Yt, mean);
+    double *ysum = reinterpret_cast<double *>(base + yt_bytes + mean_bytes);
+    double *yysum = reinterpret_cast<double *>(base + yt_bytes + mean_bytes + sums_bytes);
+    uint8_t *tables = base + yt_bytes + mean_bytes + 2 * sums_bytes;
+    st = launch_target_store(ctx, Y_tgt, N_tgt, L, tau, Tp, prec, Yt, mean, ysum, yysum);
     if (st != EDM_OK) return st;
     for (int c0 = 0; c0 < N_lib; c0 += chunk) {
         const int nlib = std::min(chunk, N_lib - c0);
         st = launch_ccm_tables(ctx, X_lib, c0, nlib, L, E_lib, tau, Tp, tables, slot);
         if (st != EDM_OK) return st;
-        st = launch_lookup(ctx, Yt, N_tgt, L, tables, slot, E_lib, c0, nlib, tau, Tp, prec,
-                           rho + static_cast<size_t>(c0) * N_tgt, N_tgt);
+        st = launch_lookup(ctx, Yt, N_tgt, L, tables, slot, E_lib, c0, nlib, tau, Tp, prec, ysum,
+                           yysum, rho + static_cast<size_t>(c0) * N_tgt, N_tgt);
         if (st != EDM_OK) return st;
     }
     return EDM_OK;

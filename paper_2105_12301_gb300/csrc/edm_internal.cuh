@@ -53,13 +53,10 @@ edm_status after_launch(edm_ctx *ctx, const char *kernel);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Layout of one row of a CCM neighbour table: k uint16 neighbour rows
-// (already shifted by Tp), padded to 16 bytes, then k float32 normalised
-// weights, padded to 16 bytes.
-__host__ __device__ inline int table_idx_bytes(int k) { return ((2 * k + 15) / 16) * 16; }
-__host__ __device__ inline int table_row_bytes(int k) {
-    return table_idx_bytes(k) + ((4 * k + 15) / 16) * 16;
-}
+// Layout of one row of a CCM neighbour table (k = E+1 neighbours): the
+// first k-1 normalised weights as float32 (the k-th is 1 minus their sum),
+// then the k neighbour rows (time index + Tp) as uint16, padded to 16 bytes.
+__host__ __device__ constexpr int table_row_bytes(int k) { return ((4 * (k - 1) + 2 * k + 15) / 16) * 16; }
 
 // Launchers (one translation unit each).
 edm_status launch_embed(edm_ctx *ctx, const float *x, int L, int E, int tau, float *out);
@@ -70,12 +67,16 @@ edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, int lib0, int nlib, i
                              size_t slot_bytes);
 edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max, int tau,
                           int Tp_sel, int32_t *E_opt, float *rho_E);
-edm_status launch_target_store(edm_ctx *ctx, const float *Y, int N_tgt, int L,
-                               edm_precision prec, uint8_t *Yt, double *mean_ws);
+// Transposed, centred target tiles plus, per E = 1..EDM_E_MAX, the FP64 sums
+// of the stored values and of their squares over the observation window of
+// E (times (E-1)tau+Tp .. L-1): ysum / yysum [EDM_E_MAX][N_tgt].
+edm_status launch_target_store(edm_ctx *ctx, const float *Y, int N_tgt, int L, int tau, int Tp,
+                               edm_precision prec, uint8_t *Yt, double *mean_ws, double *ysum,
+                               double *yysum);
 edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L,
                          const uint8_t *tables, size_t slot_bytes, const int32_t *E_lib,
                          int lib0, int nlib, int tau, int Tp, edm_precision prec,
-                         float *rho, long long rho_ld);
+                         const double *ysum, const double *yysum, float *rho, long long rho_ld);
 edm_status launch_smem_probe(edm_ctx *ctx, double ms, double *bytes_per_s);
 size_t simplex_workspace_bytes(edm_ctx *ctx, int N, int L, int E_max);
 size_t ccm_slot_bytes(int L, int tau, int Tp);

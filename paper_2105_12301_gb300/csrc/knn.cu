@@ -126,27 +126,34 @@ edm_status launch_knn(edm_ctx *ctx, const float *X, int N, int L, int E, int tau
 
 // ----------------------------------------------------- CCM neighbour tables
 
-// Rows [r0, r1) of one library's table: exact neighbours, normalised simplex
-// weights, neighbour rows pre-shifted by Tp.
+// Rows [r0, r1) of one library's table: the exact FP64 neighbour set,
+// normalised simplex weights, neighbour rows pre-shifted by Tp.
 template <int E>
 __device__ __forceinline__ void table_rows(const float *xs, int L, int tau, int Tp, int r0, int r1,
                                            WarpScratch *ws, uint8_t *slot) {
     constexpr int K = E + 1;
-    constexpr int IB = (2 * K + 15) / 16 * 16;
-    constexpr int WN = (4 * K + 15) / 16 * 4;  // weight entries incl. padding
-    constexpr int RS = IB + WN * 4;
+    constexpr int RS = table_row_bytes(K);
+    constexpr int WORDS = RS / 4;
     const int lo = (E - 1) * tau, hi = L - 1 - Tp;
     const int warp = threadIdx.x >> 5, lane = lane_id();
     for (int i = r0 + warp; i < r1; i += KNN_WARPS) {
         int u = 0;
         float d = 0.f;
-        knn_row<E, KNN_ORDERED>(xs, lo + i, lo, hi, tau, K, ws, &u, &d);
+        knn_row<E, KNN_SET>(xs, lo + i, lo, hi, tau, K, ws, &u, &d);
         const float w = simplex_weight(d, K);
-        uint8_t *row = slot + static_cast<size_t>(i) * RS;
-        uint16_t *ri = reinterpret_cast<uint16_t *>(row);
-        float *rw = reinterpret_cast<float *>(row + IB);
-        if (lane < IB / 2) ri[lane] = lane < K ? static_cast<uint16_t>(u + Tp) : 0;
-        if (lane < WN) rw[lane] = lane < K ? w : 0.f;
+        // word j < K-1: weight j; word K-1+h: rows 2h (low half) and 2h+1 (high)
+        const int h = lane - (K - 1);
+        const int ua = __shfl_sync(FULL, u, min(max(2 * h, 0), 31));
+        const int ub = __shfl_sync(FULL, u, min(max(2 * h + 1, 0), 31));
+        uint32_t word = 0;
+        if (lane < K - 1) {
+            word = __float_as_uint(w);
+        } else if (h >= 0 && 2 * h < K) {
+            word = static_cast<uint32_t>(ua + Tp) & 0xffffu;
+            if (2 * h + 1 < K) word |= (static_cast<uint32_t>(ub + Tp) & 0xffffu) << 16;
+        }
+        if (lane < WORDS)
+            reinterpret_cast<uint32_t *>(slot + static_cast<size_t>(i) * RS)[lane] = word;
     }
 }
 

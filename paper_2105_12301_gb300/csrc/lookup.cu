@@ -6,22 +6,27 @@
 // CTA owns one target tile (staged in shared memory by a bulk TMA copy) and
 // a block of libraries.  A producer warp streams the libraries' neighbour
 // tables through a ring of shared-memory stages (bulk TMA copies completing
-// on mbarriers); eight consumer warps take one table row (one query time) at
-// a time: the k (neighbour row, weight) pairs are warp-uniform broadcast
-// reads, and lane l gathers target l's value at each neighbour row -- all
-// 32 lanes read one 128-byte shared-memory row, so every gather is a single
-// conflict-free wavefront.  The prediction never leaves registers; each lane
-// accumulates the five Pearson moments of its target in FP32, the CTA sums
-// the warps' partials in FP64 and writes rho.
+// on mbarriers); sixteen consumer warps take one table row (one query time)
+// at a time: the k (neighbour row, weight) pairs are warp-uniform broadcast
+// reads (one 16-byte read for k <= 3), and lane l gathers target l's value
+// at each neighbour row -- all 32 lanes read one 128-byte shared-memory row,
+// so every gather is a single conflict-free wavefront.  The prediction never
+// leaves registers; each lane accumulates the prediction's sum, its sum of
+// squares and its cross product with the observation in FP32.  The target's
+// own sums over the observation window are precomputed in FP64 per (target,
+// E).  A finisher warp adds the consumers' partials and forms rho in FP64,
+// handed over through a pair of mbarriers so that no consumer waits for it.
 #include <cuda_bf16.h>
 
 #include "edm_internal.cuh"
 
 namespace edm {
 
-constexpr int LK_NW = 8;                       // consumer warps
-constexpr int LK_THREADS = (LK_NW + 1) * 32;   // + one producer warp
-constexpr int LK_CR = 32;                      // table rows per stage
+constexpr int LK_NC = 16;                      // consumer warps
+constexpr int LK_PRODUCER = LK_NC;             // warp issuing the bulk copies
+constexpr int LK_FINISHER = LK_NC + 1;         // warp turning moments into rho
+constexpr int LK_THREADS = (LK_NC + 2) * 32;
+constexpr int LK_STAGE_BYTES = 6144;           // table bytes per pipeline stage
 constexpr int LK_MAX_STAGES = 8;
 constexpr int LK_TILE_ROW = 128;               // bytes per time row of a tile
 
@@ -72,6 +77,54 @@ __global__ void target_store_kernel(const float *__restrict__ Y, int N, int L,
     }
 }
 
+// The stored value of target tgt at time u, as the lookup reads it.
+template <bool BF16>
+__device__ __forceinline__ float stored_target(const uint8_t *Yt, int L, int tgt, int u) {
+    constexpr int TT = BF16 ? 64 : 32;
+    const uint32_t *row = reinterpret_cast<const uint32_t *>(
+        Yt + (static_cast<size_t>(tgt / TT) * L + u) * LK_TILE_ROW);
+    if (!BF16) return __uint_as_float(row[tgt % 32]);
+    const uint32_t v = row[(tgt % 64) >> 1];
+    return __uint_as_float((tgt & 1) ? (v & 0xffff0000u) : (v << 16));
+}
+
+// One warp per target: FP64 sums of the stored values and their squares
+// over the observation window of every E, times (E-1)tau+Tp .. L-1.  The
+// windows are nested, so one pass over the longest suffix plus the pieces
+// between consecutive starts gives all of them.
+template <bool BF16>
+__global__ void target_sums_kernel(const uint8_t *__restrict__ Yt, int N, int L, int tau, int Tp,
+                                   double *__restrict__ ysum, double *__restrict__ yysum) {
+    const int tgt = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = lane_id();
+    if (tgt >= N) return;
+    int e_top = EDM_E_MAX;
+    while (e_top > 1 && (e_top - 1) * tau + Tp >= L) --e_top;
+    const int start_top = (e_top - 1) * tau + Tp;
+    double s1 = 0.0, s2 = 0.0;
+    for (int u = start_top + lane; u < L; u += 32) {
+        const double v = stored_target<BF16>(Yt, L, tgt, u);
+        s1 += v;
+        s2 += v * v;
+    }
+    s1 = warp_sum_d(s1);
+    s2 = warp_sum_d(s2);
+    if (lane != 0) return;
+    for (int E = EDM_E_MAX; E >= 1; --E) {
+        const int start = (E - 1) * tau + Tp;
+        if (E < e_top) {
+            // add times start .. start(E+1)-1
+            for (int u = start; u < E * tau + Tp && u < L; ++u) {
+                const double v = stored_target<BF16>(Yt, L, tgt, u);
+                s1 += v;
+                s2 += v * v;
+            }
+        }
+        const bool valid = start < L;
+        ysum[static_cast<size_t>(E - 1) * N + tgt] = valid ? s1 : 0.0;
+        yysum[static_cast<size_t>(E - 1) * N + tgt] = valid ? s2 : 0.0;
+    }
+}
+
 static int targets_per_tile(edm_precision prec) { return prec == EDM_BF16_TARGETS ? 64 : 32; }
 
 size_t target_store_bytes(int N_tgt, int L, edm_precision prec) {
@@ -80,20 +133,30 @@ size_t target_store_bytes(int N_tgt, int L, edm_precision prec) {
     return align_up(tiles * L * LK_TILE_ROW, 256);
 }
 
-edm_status launch_target_store(edm_ctx *ctx, const float *Y, int N_tgt, int L,
-                               edm_precision prec, uint8_t *Yt, double *mean_ws) {
+edm_status launch_target_store(edm_ctx *ctx, const float *Y, int N_tgt, int L, int tau, int Tp,
+                               edm_precision prec, uint8_t *Yt, double *mean_ws, double *ysum,
+                               double *yysum) {
+    const int warps_blocks = (N_tgt * 32 + 255) / 256;
     before_launch(ctx);
-    target_mean_kernel<<<(N_tgt * 32 + 255) / 256, 256, 0, ctx->stream>>>(Y, N_tgt, L, mean_ws);
+    target_mean_kernel<<<warps_blocks, 256, 0, ctx->stream>>>(Y, N_tgt, L, mean_ws);
     edm_status st = after_launch(ctx, "target_mean_kernel");
     if (st != EDM_OK) return st;
     const int tt = targets_per_tile(prec);
     dim3 grid((N_tgt + tt - 1) / tt, (L + 31) / 32), block(32, 8);
+    const bool bf16 = prec == EDM_BF16_TARGETS;
     before_launch(ctx);
-    if (prec == EDM_BF16_TARGETS)
+    if (bf16)
         target_store_kernel<true><<<grid, block, 0, ctx->stream>>>(Y, N_tgt, L, mean_ws, Yt);
     else
         target_store_kernel<false><<<grid, block, 0, ctx->stream>>>(Y, N_tgt, L, mean_ws, Yt);
-    return after_launch(ctx, "target_store_kernel");
+    st = after_launch(ctx, "target_store_kernel");
+    if (st != EDM_OK) return st;
+    before_launch(ctx);
+    if (bf16)
+        target_sums_kernel<true><<<warps_blocks, 256, 0, ctx->stream>>>(Yt, N_tgt, L, tau, Tp, ysum, yysum);
+    else
+        target_sums_kernel<false><<<warps_blocks, 256, 0, ctx->stream>>>(Yt, N_tgt, L, tau, Tp, ysum, yysum);
+    return after_launch(ctx, "target_sums_kernel");
 }
 
 // ------------------------------------------------------- lookup + Pearson
@@ -103,9 +166,11 @@ struct LookupArgs {
     const uint8_t *tables;
     size_t slot_bytes;
     const int32_t *E_lib;  // indexed by library id
+    const double *ysum;    // [EDM_E_MAX][N_tgt]
+    const double *yysum;
     int lib0, nlib, LB;    // libraries [lib0, lib0+nlib) of this launch; LB per CTA
     int L, tau, Tp, N_tgt;
-    int stages, stage_bytes;
+    int stages;
     float *rho;            // row of library lib0
     long long rho_ld;
     int *flags;
@@ -115,97 +180,93 @@ __device__ __forceinline__ bool lib_valid(int E, int L, int tau, int Tp) {
     return E >= 1 && E <= EDM_E_MAX && L - (E - 1) * tau - Tp >= E + 2;
 }
 
-__device__ __forceinline__ void named_bar_sync(int id, int threads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
-}
+// Rows of one table chunk: as many whole rows as fit a stage.
+__device__ __forceinline__ int chunk_rows(int K) { return LK_STAGE_BYTES / table_row_bytes(K); }
 
 template <bool BF16>
 struct Moments {
-    static constexpr int N = BF16 ? 10 : 5;
-    float m[N];
+    static constexpr int N = BF16 ? 6 : 3;  // per target: sum a, sum a^2, sum a*b
 };
 
-// Gather + accumulate for one library whose k = K is a compile-time value.
+// Gather + accumulate one library whose k = K is a compile-time value.
 template <int K, bool BF16, bool SMEM_TILE>
 __device__ __forceinline__ void consume_library(const LookupArgs &a, const uint8_t *tile,
                                                 const uint8_t *stages, uint64_t *full,
                                                 uint64_t *empty, int &seq, int n, int t0,
                                                 float (&m)[Moments<BF16>::N]) {
-    constexpr int IB = (2 * K + 15) / 16 * 16;
-    constexpr int WN = (4 * K + 15) / 16 * 4;
-    constexpr int RS = IB + WN * 4;
+    constexpr int RS = table_row_bytes(K);
+    constexpr int NV = RS / 16;          // 16-byte reads per row
+    constexpr int CR = LK_STAGE_BYTES / RS;
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const uint32_t *tl = reinterpret_cast<const uint32_t *>(tile) + lane;
-    for (int c0 = 0; c0 < n; c0 += LK_CR) {
+    for (int c0 = 0; c0 < n; c0 += CR) {
         const int s = seq % a.stages;
         const uint32_t par = (seq / a.stages) & 1;
         mbar_wait_bounded(&full[s], par, a.flags);
-        const uint8_t *st = stages + static_cast<size_t>(s) * a.stage_bytes;
-        const int rows = min(LK_CR, n - c0);
-        for (int r = warp; r < rows; r += LK_NW) {
-            const uint8_t *row = st + r * RS;
-            uint32_t ix[(K + 1) / 2];
-            float w[WN];
+        const uint8_t *st = stages + static_cast<size_t>(s) * LK_STAGE_BYTES;
+        const int rows = min(CR, n - c0);
+        for (int r = warp; r < rows; r += LK_NC) {
+            uint32_t wd[4 * NV];
 #pragma unroll
-            for (int q = 0; q < IB / 16; ++q) {
-                const uint4 v = reinterpret_cast<const uint4 *>(row)[q];
-                if (4 * q + 0 < (K + 1) / 2) ix[4 * q + 0] = v.x;
-                if (4 * q + 1 < (K + 1) / 2) ix[4 * q + 1] = v.y;
-                if (4 * q + 2 < (K + 1) / 2) ix[4 * q + 2] = v.z;
-                if (4 * q + 3 < (K + 1) / 2) ix[4 * q + 3] = v.w;
+            for (int q = 0; q < NV; ++q) {
+                const uint4 v = reinterpret_cast<const uint4 *>(st + r * RS)[q];
+                wd[4 * q + 0] = v.x;
+                wd[4 * q + 1] = v.y;
+                wd[4 * q + 2] = v.z;
+                wd[4 * q + 3] = v.w;
             }
+            float wl = 1.f;  // weight of the last neighbour: 1 - sum of the others
 #pragma unroll
-            for (int q = 0; q < WN / 4; ++q) {
-                const float4 v = reinterpret_cast<const float4 *>(row + IB)[q];
-                w[4 * q + 0] = v.x;
-                w[4 * q + 1] = v.y;
-                w[4 * q + 2] = v.z;
-                w[4 * q + 3] = v.w;
-            }
+            for (int q = 0; q < K - 1; ++q) wl -= __uint_as_float(wd[q]);
             const int yrow = t0 + c0 + r + a.Tp;
             if (!BF16) {
                 float acc = 0.f;
 #pragma unroll
                 for (int q = 0; q < K; ++q) {
-                    const uint32_t u = (q & 1) ? (ix[q >> 1] >> 16) : (ix[q >> 1] & 0xffffu);
+                    const uint32_t hw = wd[K - 1 + (q >> 1)];
+                    const uint32_t u = (q & 1) ? (hw >> 16) : (hw & 0xffffu);
                     const float v = SMEM_TILE ? __uint_as_float(tl[u * 32])
                                               : __uint_as_float(__ldg(tl + u * 32));
-                    acc = __fmaf_rn(w[q], v, acc);
+                    const float w = (q < K - 1) ? __uint_as_float(wd[q]) : wl;
+                    acc = __fmaf_rn(w, v, acc);
                 }
                 const float y = SMEM_TILE ? __uint_as_float(tl[yrow * 32])
                                           : __uint_as_float(__ldg(tl + yrow * 32));
                 m[0] += acc;
-                m[1] += y;
-                m[2] = __fmaf_rn(acc, acc, m[2]);
-                m[3] = __fmaf_rn(y, y, m[3]);
-                m[4] = __fmaf_rn(acc, y, m[4]);
+                m[1] = __fmaf_rn(acc, acc, m[1]);
+                m[2] = __fmaf_rn(acc, y, m[2]);
             } else {
                 float acc0 = 0.f, acc1 = 0.f;
 #pragma unroll
                 for (int q = 0; q < K; ++q) {
-                    const uint32_t u = (q & 1) ? (ix[q >> 1] >> 16) : (ix[q >> 1] & 0xffffu);
+                    const uint32_t hw = wd[K - 1 + (q >> 1)];
+                    const uint32_t u = (q & 1) ? (hw >> 16) : (hw & 0xffffu);
                     const uint32_t v = SMEM_TILE ? tl[u * 32] : __ldg(tl + u * 32);
-                    acc0 = __fmaf_rn(w[q], __uint_as_float(v << 16), acc0);
-                    acc1 = __fmaf_rn(w[q], __uint_as_float(v & 0xffff0000u), acc1);
+                    const float w = (q < K - 1) ? __uint_as_float(wd[q]) : wl;
+                    acc0 = __fmaf_rn(w, __uint_as_float(v << 16), acc0);
+                    acc1 = __fmaf_rn(w, __uint_as_float(v & 0xffff0000u), acc1);
                 }
                 const uint32_t yv = SMEM_TILE ? tl[yrow * 32] : __ldg(tl + yrow * 32);
                 const float y0 = __uint_as_float(yv << 16), y1 = __uint_as_float(yv & 0xffff0000u);
                 m[0] += acc0;
-                m[1] += y0;
-                m[2] = __fmaf_rn(acc0, acc0, m[2]);
-                m[3] = __fmaf_rn(y0, y0, m[3]);
-                m[4] = __fmaf_rn(acc0, y0, m[4]);
-                m[5] += acc1;
-                m[6] += y1;
-                m[7] = __fmaf_rn(acc1, acc1, m[7]);
-                m[8] = __fmaf_rn(y1, y1, m[8]);
-                m[9] = __fmaf_rn(acc1, y1, m[9]);
+                m[1] = __fmaf_rn(acc0, acc0, m[1]);
+                m[2] = __fmaf_rn(acc0, y0, m[2]);
+                m[3] += acc1;
+                m[4] = __fmaf_rn(acc1, acc1, m[4]);
+                m[5] = __fmaf_rn(acc1, y1, m[5]);
             }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         ++seq;
     }
+}
+
+// rho from the prediction moments (FP32 partials of the consumer warps) and
+// the target's FP64 window sums.
+__device__ __forceinline__ float finish_rho(double n, double sa, double saa, double sab, double sb,
+                                            double sbb) {
+    return static_cast<float>(pearson_from_moments(n, sa, sb, saa, sbb, sab));
 }
 
 template <bool BF16, bool SMEM_TILE>
@@ -220,29 +281,35 @@ __global__ void __launch_bounds__(LK_THREADS, 1) lookup_kernel(const LookupArgs 
     const uint8_t *tile_g = a.Yt + static_cast<size_t>(tile_id) * tile_bytes;
     uint8_t *tile_s = smem;
     uint8_t *stages = smem + (SMEM_TILE ? tile_bytes : 0);
-    float *red = reinterpret_cast<float *>(stages + static_cast<size_t>(a.stages) * a.stage_bytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(red + 2 * LK_NW * NM * 32);
+    float *red = reinterpret_cast<float *>(stages + static_cast<size_t>(a.stages) * LK_STAGE_BYTES);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(red + 2 * LK_NC * NM * 32);
     uint64_t *full = bars, *empty = bars + a.stages, *tbar = bars + 2 * a.stages;
+    uint64_t *red_full = tbar + 1, *red_empty = tbar + 3;
     const int warp = threadIdx.x >> 5, lane = lane_id();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], LK_NW);
+            mbar_init(&empty[s], LK_NC);
         }
         mbar_init(tbar, 1);
+        for (int p = 0; p < 2; ++p) {
+            mbar_init(&red_full[p], LK_NC);
+            mbar_init(&red_empty[p], 1);
+        }
         fence_barrier_init();
     }
     __syncthreads();
 
-    if (warp == LK_NW) {
+    if (warp == LK_PRODUCER) {
         // ---------------- producer: target tile, then the table stream
         if (lane == 0) {
             if (SMEM_TILE) {
                 mbar_arrive_expect_tx(tbar, static_cast<uint32_t>(tile_bytes));
                 for (size_t off = 0; off < tile_bytes; off += 32768)
                     bulk_copy_g2s(tile_s + off, tile_g + off,
-                                  static_cast<uint32_t>(tile_bytes - off < 32768 ? tile_bytes - off : 32768), tbar);
+                                  static_cast<uint32_t>(tile_bytes - off < 32768 ? tile_bytes - off : 32768),
+                                  tbar);
             }
             int seq = 0;
             for (int lib = lb0; lib < lb1; ++lib) {
@@ -250,17 +317,62 @@ __global__ void __launch_bounds__(LK_THREADS, 1) lookup_kernel(const LookupArgs 
                 if (!lib_valid(E, a.L, a.tau, a.Tp)) continue;
                 const int n = a.L - (E - 1) * a.tau - a.Tp;
                 const int RS = table_row_bytes(E + 1);
+                const int CR = chunk_rows(E + 1);
                 const uint8_t *slot = a.tables + static_cast<size_t>(lib - a.lib0) * a.slot_bytes;
-                for (int c0 = 0; c0 < n; c0 += LK_CR) {
+                for (int c0 = 0; c0 < n; c0 += CR) {
                     const int s = seq % a.stages, j = seq / a.stages;
                     if (j > 0) mbar_wait_bounded(&empty[s], (j - 1) & 1, a.flags);
-                    const uint32_t bytes = static_cast<uint32_t>(min(LK_CR, n - c0) * RS);
+                    const uint32_t bytes = static_cast<uint32_t>(min(CR, n - c0) * RS);
                     mbar_arrive_expect_tx(&full[s], bytes);
-                    bulk_copy_g2s(stages + static_cast<size_t>(s) * a.stage_bytes,
+                    bulk_copy_g2s(stages + static_cast<size_t>(s) * LK_STAGE_BYTES,
                                   slot + static_cast<size_t>(c0) * RS, bytes, &full[s]);
                     ++seq;
                 }
             }
+        }
+        return;
+    }
+
+    if (warp == LK_FINISHER) {
+        // ---------------- finisher: rho of every library of this CTA
+        int done = 0;
+        for (int lib = lb0; lib < lb1; ++lib) {
+            const int E = a.E_lib[lib];
+            float *rho_row = a.rho + static_cast<long long>(lib - a.lib0) * a.rho_ld;
+            if (!lib_valid(E, a.L, a.tau, a.Tp)) {
+                for (int j = lane; j < TT; j += 32) {
+                    const int tgt = tile_id * TT + j;
+                    if (tgt < a.N_tgt) rho_row[tgt] = __int_as_float(0x7fc00000);
+                }
+                if (lane == 0 && blockIdx.x == 0) set_flag(a.flags, EDMF_BADARG);
+                continue;
+            }
+            const int p = done & 1;
+            mbar_wait_bounded(&red_full[p], (done >> 1) & 1, a.flags);
+            const float *base = red + p * LK_NC * NM * 32;
+            float S[NM];
+#pragma unroll
+            for (int j = 0; j < NM; ++j) S[j] = 0.f;
+            for (int w = 0; w < LK_NC; ++w)
+#pragma unroll
+                for (int j = 0; j < NM; ++j) S[j] += base[(w * NM + j) * 32 + lane];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&red_empty[p]);
+            const double dn = static_cast<double>(a.L - (E - 1) * a.tau - a.Tp);
+            const size_t wo = static_cast<size_t>(E - 1) * a.N_tgt;
+            if (!BF16) {
+                const int tgt = tile_id * 32 + lane;
+                if (tgt < a.N_tgt)
+                    rho_row[tgt] = finish_rho(dn, S[0], S[1], S[2], a.ysum[wo + tgt], a.yysum[wo + tgt]);
+            } else {
+                const int tgt = tile_id * 64 + 2 * lane;
+                if (tgt < a.N_tgt)
+                    rho_row[tgt] = finish_rho(dn, S[0], S[1], S[2], a.ysum[wo + tgt], a.yysum[wo + tgt]);
+                if (tgt + 1 < a.N_tgt)
+                    rho_row[tgt + 1] = finish_rho(dn, S[3], S[4], S[5], a.ysum[wo + tgt + 1],
+                                                  a.yysum[wo + tgt + 1]);
+            }
+            ++done;
         }
         return;
     }
@@ -272,17 +384,7 @@ __global__ void __launch_bounds__(LK_THREADS, 1) lookup_kernel(const LookupArgs 
     float m[NM];
     for (int lib = lb0; lib < lb1; ++lib) {
         const int E = a.E_lib[lib];
-        float *rho_row = a.rho + static_cast<long long>(lib - a.lib0) * a.rho_ld;
-        if (!lib_valid(E, a.L, a.tau, a.Tp)) {
-            if (warp == 0) {
-                for (int j = lane; j < TT; j += 32) {
-                    const int tgt = tile_id * TT + j;
-                    if (tgt < a.N_tgt) rho_row[tgt] = __int_as_float(0x7fc00000);
-                }
-                if (lane == 0 && blockIdx.x == 0) set_flag(a.flags, EDMF_BADARG);
-            }
-            continue;
-        }
+        if (!lib_valid(E, a.L, a.tau, a.Tp)) continue;
         const int n = a.L - (E - 1) * a.tau - a.Tp, t0 = (E - 1) * a.tau;
 #pragma unroll
         for (int j = 0; j < NM; ++j) m[j] = 0.f;
@@ -296,56 +398,38 @@ __global__ void __launch_bounds__(LK_THREADS, 1) lookup_kernel(const LookupArgs 
 #undef EDM_CASE
         default: break;
         }
-        // cross-warp reduction (double-buffered by library parity)
-        float *rb = red + ((done & 1) * LK_NW + warp) * NM * 32;
+        // hand the partial moments to the finisher (double-buffered)
+        const int p = done & 1;
+        if (done >= 2) mbar_wait_bounded(&red_empty[p], ((done >> 1) - 1) & 1, a.flags);
+        float *rb = red + (p * LK_NC + warp) * NM * 32;
 #pragma unroll
         for (int j = 0; j < NM; ++j) rb[j * 32 + lane] = m[j];
-        named_bar_sync(1, LK_NW * 32);
-        if (warp == 0) {
-            const float *base = red + (done & 1) * LK_NW * NM * 32;
-            double S[NM];
-#pragma unroll
-            for (int j = 0; j < NM; ++j) S[j] = 0.0;
-            for (int w = 0; w < LK_NW; ++w)
-#pragma unroll
-                for (int j = 0; j < NM; ++j) S[j] += static_cast<double>(base[(w * NM + j) * 32 + lane]);
-            const double dn = static_cast<double>(n);
-            if (!BF16) {
-                const int tgt = tile_id * 32 + lane;
-                if (tgt < a.N_tgt)
-                    rho_row[tgt] = static_cast<float>(pearson_from_moments(dn, S[0], S[1], S[2], S[3], S[4]));
-            } else {
-                const int tgt = tile_id * 64 + 2 * lane;
-                if (tgt < a.N_tgt)
-                    rho_row[tgt] = static_cast<float>(pearson_from_moments(dn, S[0], S[1], S[2], S[3], S[4]));
-                if (tgt + 1 < a.N_tgt)
-                    rho_row[tgt + 1] =
-                        static_cast<float>(pearson_from_moments(dn, S[5], S[6], S[7], S[8], S[9]));
-            }
-        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&red_full[p]);
         ++done;
     }
 }
 
 edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, const uint8_t *tables,
                          size_t slot_bytes, const int32_t *E_lib, int lib0, int nlib, int tau,
-                         int Tp, edm_precision prec, float *rho, long long rho_ld) {
+                         int Tp, edm_precision prec, const double *ysum, const double *yysum,
+                         float *rho, long long rho_ld) {
     const bool bf16 = prec == EDM_BF16_TARGETS;
     const int tt = targets_per_tile(prec);
     const int n_tiles = (N_tgt + tt - 1) / tt;
-    const int nm = bf16 ? 10 : 5;
+    const int nm = bf16 ? 6 : 3;
     const size_t tile_bytes = static_cast<size_t>(L) * LK_TILE_ROW;
-    const int stage_bytes = LK_CR * table_row_bytes(EDM_E_MAX + 1);
-    const size_t fixed = static_cast<size_t>(2) * LK_NW * nm * 32 * sizeof(float) +
-                         (2 * LK_MAX_STAGES + 1) * sizeof(uint64_t);
+    const size_t fixed = static_cast<size_t>(2) * LK_NC * nm * 32 * sizeof(float) +
+                         (2 * LK_MAX_STAGES + 5) * sizeof(uint64_t);
     const size_t limit = static_cast<size_t>(ctx->max_smem_optin);
-    bool smem_tile = tile_bytes + fixed + 2 * stage_bytes <= limit && tile_bytes < (1u << 20);
+    const bool smem_tile =
+        tile_bytes + fixed + 2 * LK_STAGE_BYTES <= limit && tile_bytes < (1u << 20);
     const size_t avail = limit - fixed - (smem_tile ? tile_bytes : 0);
-    const int stages = static_cast<int>(std::min<size_t>(LK_MAX_STAGES, avail / stage_bytes));
+    const int stages = static_cast<int>(std::min<size_t>(LK_MAX_STAGES, avail / LK_STAGE_BYTES));
     if (stages < 2) return set_error(ctx, EDM_ERR_INTERNAL, "lookup: no room for table stages");
-    const size_t smem = (smem_tile ? tile_bytes : 0) + static_cast<size_t>(stages) * stage_bytes +
-                        static_cast<size_t>(2) * LK_NW * nm * 32 * sizeof(float) +
-                        (2 * stages + 1) * sizeof(uint64_t);
+    const size_t smem = (smem_tile ? tile_bytes : 0) + static_cast<size_t>(stages) * LK_STAGE_BYTES +
+                        static_cast<size_t>(2) * LK_NC * nm * 32 * sizeof(float) +
+                        (2 * stages + 5) * sizeof(uint64_t);
 
     // libraries per CTA: enough CTAs for balance, enough libraries per CTA to
     // amortise the tile load
@@ -357,6 +441,8 @@ edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, cons
     a.tables = tables;
     a.slot_bytes = slot_bytes;
     a.E_lib = E_lib;
+    a.ysum = ysum;
+    a.yysum = yysum;
     a.lib0 = lib0;
     a.nlib = nlib;
     a.LB = static_cast<int>(lb);
@@ -365,7 +451,6 @@ edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, cons
     a.Tp = Tp;
     a.N_tgt = N_tgt;
     a.stages = stages;
-    a.stage_bytes = stage_bytes;
     a.rho = rho;
     a.rho_ld = rho_ld;
     a.flags = ctx->d_flags;

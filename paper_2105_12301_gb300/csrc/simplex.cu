@@ -100,6 +100,181 @@ __global__ void __launch_bounds__(SX_WARPS * 32)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Incremental sweep over E (series of up to 32*CH points).
+//
+// A warp owns one query time t and keeps the FP32 squared distance from x(t)
+// to every candidate u = lane + 32 j in registers.  Going from E-1 to E adds
+// one lag: s = fma(d, d, s) with d = X[t-(E-1)tau] - X[u-(E-1)tau], which is
+// exactly the operation sequence of the direct sum over l = 0..E-1, so the
+// values are bit-identical to those of knn_row.  Candidates below the first
+// point of P_E, past its last point, or equal to t hold +inf.  Each E then
+// selects from the registers: lane minimum, the (K+1)-th smallest of the 32
+// minima as a bound, ballot-compaction of every value at or below it into
+// the warp buffer, exact ranking of the few collected keys, and the FP64
+// band check of knn_row's KNN_SET mode.
+
+#define SX_INF __int_as_float(0x7f800000)
+
+// Ascending bitonic sort of one float per lane; value at position r.
+__device__ __forceinline__ float warp_sorted_at_f(float v, int r) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const float o = __shfl_xor_sync(FULL, v, j);
+            const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+            v = (lower == up) ? fminf(v, o) : fmaxf(v, o);
+        }
+    }
+    return __shfl_sync(FULL, v, r);
+}
+
+// Compact the keys (s[j], lane+32j) with s[j] <= bound (and finite, i.e. a
+// candidate of P_E) into ws->key; returns
+// how many there are (only the first KNN_CAP are stored).
+template <int CH>
+__device__ __forceinline__ int compact_le(const float (&s)[CH], float bound, WarpScratch *ws) {
+    const int lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    int base = 0;
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+        const bool p = s[j] <= bound && s[j] != SX_INF;
+        const unsigned b = __ballot_sync(FULL, p);
+        if (b) {
+            if (p) {
+                const int pos = base + __popc(b & lt);
+                if (pos < KNN_CAP) ws->key[pos] = mk_key(s[j], lane + 32 * j);
+            }
+            base += __popc(b);
+        }
+    }
+    __syncwarp();
+    return base;
+}
+
+template <int CH>
+__device__ __forceinline__ void sweep_row(const float *xs, int t, int hi, int E_max, int tau,
+                                          int Tp, float mu, WarpScratch *ws, float (&m)[5]) {
+    const int lane = lane_id();
+    float s[CH];
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+        const int u = lane + 32 * j;
+        s[j] = (u <= hi && u != t) ? 0.f : SX_INF;
+    }
+    for (int E = 1; E <= E_max; ++E) {
+        const int lo = (E - 1) * tau;
+        if (t < lo || hi - lo + 1 < E + 2) break;
+        const int K = E + 1;
+        // extend every distance by the lag E-1
+        const float qv = xs[t - lo];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            const int u = lane + 32 * j;
+            const float d = __fsub_rn(qv, xs[max(u - lo, 0)]);
+            const float v = __fmaf_rn(d, d, s[j]);
+            s[j] = (u < lo) ? SX_INF : v;
+        }
+        const int nc = hi - lo;
+        const int R = min(K + 1, nc);
+        float lmin = SX_INF;
+#pragma unroll
+        for (int j = 0; j < CH; ++j) lmin = fminf(lmin, s[j]);
+        const float theta = warp_sorted_at_f(lmin, R - 1);
+        int c = compact_le<CH>(s, theta, ws);
+        int u_out = 0;
+        float d_out = 0.f;
+        bool done = false;
+        if (c <= KNN_CAP) {
+            rank_keys(ws, c, R);
+            const float edge = band_edge(key_s(ws->sel[K - 1]), E);
+            if (R <= K || key_s(ws->sel[K]) > edge) {
+                if (lane < K) {
+                    const uint64_t k = ws->sel[lane];
+                    u_out = key_u(k);
+                    d_out = sqrtf(key_s(k));
+                }
+                done = true;
+            } else {
+                // resolve the band in FP64
+                c = compact_le<CH>(s, edge, ws);
+                if (c <= KNN_CAP) {
+                    rank_band_fp64(xs, t, E, tau, ws, c, K);
+                } else {
+                    brute_fp64(xs, t, lo, hi, E, tau, ws, K);
+                }
+                if (lane < K) {
+                    u_out = ws->sel_u[lane];
+                    d_out = __double2float_rn(__dsqrt_rn(ws->sel_s64[lane]));
+                }
+                done = true;
+            }
+        }
+        if (!done) {
+            // more than KNN_CAP values tie at the bound (long runs of repeats)
+            brute_fp64(xs, t, lo, hi, E, tau, ws, K);
+            if (lane < K) {
+                u_out = ws->sel_u[lane];
+                d_out = __double2float_rn(__dsqrt_rn(ws->sel_s64[lane]));
+            }
+        }
+        __syncwarp();
+        const float w = simplex_weight(d_out, K);
+        const float part = lane < K ? w * __fsub_rn(xs[u_out + Tp], mu) : 0.f;
+        const float a = warp_sum(part);
+        const float b = __fsub_rn(xs[t + Tp], mu);
+        if (lane == E - 1) {
+            m[0] += a;
+            m[1] += b;
+            m[2] = __fmaf_rn(a, a, m[2]);
+            m[3] = __fmaf_rn(b, b, m[3]);
+            m[4] = __fmaf_rn(a, b, m[4]);
+        }
+    }
+}
+
+// One CTA per series (series staged in shared memory, zero-padded to 32*CH
+// points); warps take query times t = warp, warp + SX_WARPS, ...
+template <int CH>
+__global__ void __launch_bounds__(SX_WARPS * 32)
+    sweep_kernel(const float *__restrict__ X, int L, int E_max, int tau, int Tp, int TB, int nrb,
+                 double *__restrict__ partial) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    WarpScratch *wsa = reinterpret_cast<WarpScratch *>(smem);
+    float *red = reinterpret_cast<float *>(smem + SX_WARPS * sizeof(WarpScratch));
+    double *mu_s = reinterpret_cast<double *>(red + SX_WARPS * 32 * 5);
+    float *xs = reinterpret_cast<float *>(mu_s + SX_WARPS);
+    const int series = blockIdx.x, rb = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const float *xg = X + static_cast<size_t>(series) * L;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) acc += static_cast<double>(xg[i]);
+    acc = warp_sum_d(acc);
+    if (lane == 0) mu_s[warp] = acc;
+    for (int i = threadIdx.x; i < 32 * CH; i += blockDim.x) xs[i] = i < L ? xg[i] : 0.f;
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < SX_WARPS; ++w) tot += mu_s[w];
+    const float mu = static_cast<float>(tot / L);
+    float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    WarpScratch *ws = wsa + warp;
+    const int hi = L - 1 - Tp;
+    const int t1 = min(hi + 1, (rb + 1) * TB);
+    for (int t = rb * TB + warp; t < t1; t += SX_WARPS) sweep_row<CH>(xs, t, hi, E_max, tau, Tp, mu, ws, m);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) red[(warp * 32 + lane) * 5 + j] = m[j];
+    __syncthreads();
+    for (int i = threadIdx.x; i < E_max * 5; i += blockDim.x) {
+        const int e = i / 5, j = i % 5;
+        double sum = 0.0;
+        for (int w = 0; w < SX_WARPS; ++w) sum += static_cast<double>(red[(w * 32 + e) * 5 + j]);
+        partial[((static_cast<size_t>(series) * nrb + rb) * E_max + e) * 5 + j] = sum;
+    }
+}
+
 // One thread per series: sum the partials, rho per E, argmax.
 __global__ void simplex_finish_kernel(const double *__restrict__ partial, int N, int L, int E_max,
                                       int tau, int Tp, int nrb, int32_t *__restrict__ E_opt,
@@ -151,24 +326,48 @@ edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max,
     edm_status st = ws_reserve(ctx, simplex_workspace_bytes(ctx, N, L, E_max));
     if (st != EDM_OK) return st;
     double *partial = static_cast<double *>(ctx->ws);
-    const bool smem_series = sizeof(float) * static_cast<size_t>(L) <= SX_SERIES_SMEM_MAX;
-    const size_t smem = SX_WARPS * sizeof(WarpScratch) + SX_WARPS * 32 * 5 * sizeof(float) +
-                        SX_WARPS * sizeof(double) +
-                        (smem_series ? align_up(sizeof(float) * L, 16) : 0);
+    const size_t fixed = SX_WARPS * sizeof(WarpScratch) + SX_WARPS * 32 * 5 * sizeof(float) +
+                         SX_WARPS * sizeof(double);
     dim3 grid(N, nrb);
-    if (smem_series) {
-        auto kern = simplex_kernel<true>;
+    const int ch = (L + 31) / 32;
+    if (ch <= 64) {
+        // incremental sweep with register-resident distances
+        const int CHs[] = {8, 16, 24, 32, 48, 64};
+        int CH = 64;
+        for (int c : CHs)
+            if (c >= ch) { CH = c; break; }
+        const size_t smem = fixed + sizeof(float) * 32 * CH;
+        void (*kern)(const float *, int, int, int, int, int, int, double *) = nullptr;
+        switch (CH) {
+        case 8: kern = sweep_kernel<8>; break;
+        case 16: kern = sweep_kernel<16>; break;
+        case 24: kern = sweep_kernel<24>; break;
+        case 32: kern = sweep_kernel<32>; break;
+        case 48: kern = sweep_kernel<48>; break;
+        default: kern = sweep_kernel<64>; break;
+        }
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         before_launch(ctx);
         kern<<<grid, SX_WARPS * 32, smem, ctx->stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial);
+        st = after_launch(ctx, "sweep_kernel");
+        if (st != EDM_OK) return st;
     } else {
-        auto kern = simplex_kernel<false>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        before_launch(ctx);
-        kern<<<grid, SX_WARPS * 32, smem, ctx->stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial);
+        const bool smem_series = sizeof(float) * static_cast<size_t>(L) <= SX_SERIES_SMEM_MAX;
+        const size_t smem = fixed + (smem_series ? align_up(sizeof(float) * L, 16) : 0);
+        if (smem_series) {
+            auto kern = simplex_kernel<true>;
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            before_launch(ctx);
+            kern<<<grid, SX_WARPS * 32, smem, ctx->stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial);
+        } else {
+            auto kern = simplex_kernel<false>;
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            before_launch(ctx);
+            kern<<<grid, SX_WARPS * 32, smem, ctx->stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial);
+        }
+        st = after_launch(ctx, "simplex_kernel");
+        if (st != EDM_OK) return st;
     }
-    st = after_launch(ctx, "simplex_kernel");
-    if (st != EDM_OK) return st;
     before_launch(ctx);
     simplex_finish_kernel<<<(N + 127) / 128, 128, 0, ctx->stream>>>(partial, N, L, E_max, tau,
                                                                       Tp_sel, nrb, E_opt, rho_E);

@@ -71,8 +71,14 @@ def load():
     lib.edm_simplex_optimal_E.argtypes = [vp, vp, ci, ci, ci, ci, ci, vp, vp]
     lib.edm_ccm_all.argtypes = [vp, vp, ci, vp, ci, ci, vp, ci, ci, ci, vp]
     lib.edm_ccm_batched.argtypes = [vp, ctypes.POINTER(edm_instance), ci, ci]
+    lib.edm_profile_enable.argtypes = [vp, ci]
+    lib.edm_profile_read.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ci)]
+    lib.edm_probe_smem_bandwidth.argtypes = [vp, ctypes.c_double,
+                                             ctypes.POINTER(ctypes.c_double)]
     for f in ("edm_create", "edm_destroy", "edm_set_stream", "edm_ctx_sync", "edm_embed",
-              "edm_knn", "edm_simplex_optimal_E", "edm_ccm_all", "edm_ccm_batched"):
+              "edm_knn", "edm_simplex_optimal_E", "edm_ccm_all", "edm_ccm_batched",
+              "edm_profile_enable", "edm_profile_read", "edm_probe_smem_bandwidth"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -126,6 +132,33 @@ def edm_ctx_sync(device=None):
 def edm_kernel_launches(device=None):
     dev = device if device is not None else torch.cuda.current_device()
     return int(load().edm_kernel_launches(_ctx(dev)))
+
+
+def edm_profile_enable(on, device=None):
+    """Start (clearing the record) or stop per-kernel CUDA-event timing."""
+    dev = device if device is not None else torch.cuda.current_device()
+    ctx = _ctx(dev)
+    _check(ctx, load().edm_profile_enable(ctx, 1 if on else 0), "edm_profile_enable")
+
+
+def edm_profile_read(kernel, device=None):
+    """(summed milliseconds, launches) of the recorded launches of `kernel`."""
+    dev = device if device is not None else torch.cuda.current_device()
+    ctx = _ctx(dev)
+    ms, n = ctypes.c_double(), ctypes.c_int()
+    _check(ctx, load().edm_profile_read(ctx, kernel.encode(), ctypes.byref(ms), ctypes.byref(n)),
+           "edm_profile_read")
+    return ms.value, n.value
+
+
+def edm_probe_smem_bandwidth(ms=200.0, device=None):
+    """Measured shared-memory gather bandwidth of the GPU, bytes/s."""
+    dev = device if device is not None else torch.cuda.current_device()
+    ctx = _ctx(dev)
+    bw = ctypes.c_double()
+    _check(ctx, load().edm_probe_smem_bandwidth(ctx, float(ms), ctypes.byref(bw)),
+           "edm_probe_smem_bandwidth")
+    return bw.value
 
 
 def edm_embed(x, E, tau=1):

@@ -135,9 +135,9 @@ def config2(N=1000, L=1000):
     return coupled_logistic(N, L, 1002, 3.6, 3.9, 0.05, 0.1, noise=0.01)
 
 
-def config3(N=50000, L=1500):
+def config3(N=50000, L=1500, seed=1003):
     """Calcium-imaging-shaped all-to-all workload, 50,000 x 1,500."""
-    return calcium_lorenz(N, L, 1003)
+    return calcium_lorenz(N, L, seed)
 
 
 def config4_shapes(n_inst=256, seed=1004):
