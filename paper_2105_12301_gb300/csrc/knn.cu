@@ -193,6 +193,75 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
     }
 }
 
+// Register-resident variant for series of up to 32*CH points: the FP32
+// distances from x(t) to every candidate are accumulated lag by lag in
+// registers (lag order 0..E-1, the same operations as dist32) and the
+// neighbours are selected from registers (select_set_regs), one pass over
+// the candidates.  HEAD1: every lag offset (E-1)tau is below 32, so only
+// candidate slot 0 can reach before the start of the series.
+template <int CH, bool HEAD1>
+__global__ void __launch_bounds__(KNN_WARPS * 32)
+    ccm_table_regs_kernel(const float *__restrict__ X, int lib0, int L,
+                          const int32_t *__restrict__ E_lib, int tau, int Tp, int RB,
+                          uint8_t *__restrict__ tables, size_t slot_bytes, int *flags) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    WarpScratch *wsa = reinterpret_cast<WarpScratch *>(smem);
+    float *xs = reinterpret_cast<float *>(smem + KNN_WARPS * sizeof(WarpScratch));
+    const int lib = lib0 + blockIdx.x;
+    const int E = E_lib[lib];
+    if (!ccm_E_valid(E, L, tau, Tp)) {
+        if (blockIdx.y == 0 && threadIdx.x == 0) set_flag(flags, EDMF_BADARG);
+        return;
+    }
+    const int K = E + 1;
+    const int lo = (E - 1) * tau, hi = L - 1 - Tp, n = hi - lo + 1;
+    const int r0 = blockIdx.y * RB, r1 = min(n, r0 + RB);
+    if (r0 >= r1) return;
+    const float *xg = X + static_cast<size_t>(lib) * L;
+    for (int i = threadIdx.x; i < 32 * CH; i += blockDim.x) xs[i] = i < L ? xg[i] : 0.f;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    WarpScratch *ws = wsa + warp;
+    uint8_t *slot = tables + static_cast<size_t>(blockIdx.x) * slot_bytes;
+    const int RS = table_row_bytes(K), WORDS = RS / 4;
+    for (int i = r0 + warp; i < r1; i += KNN_WARPS) {
+        const int t = lo + i;
+        float s[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            const int u = lane + 32 * j;
+            s[j] = (u >= lo && u <= hi && u != t) ? 0.f : EDM_INF;
+        }
+        for (int l = 0; l < E; ++l) {
+            const int off = l * tau;
+            const float q = xs[t - off];
+#pragma unroll
+            for (int j = 0; j < CH; ++j) {
+                const int u = lane + 32 * j;
+                const float x = (!HEAD1 || j == 0) ? xs[max(u - off, 0)] : xs[u - off];
+                const float d = __fsub_rn(q, x);
+                s[j] = __fmaf_rn(d, d, s[j]);
+            }
+        }
+        int u = 0;
+        float d = 0.f;
+        select_set_regs<CH>(s, xs, t, lo, hi, E, tau, K, ws, u, d);
+        const float w = simplex_weight(d, K);
+        const int h = lane - (K - 1);
+        const int ua = __shfl_sync(FULL, u, min(max(2 * h, 0), 31));
+        const int ub = __shfl_sync(FULL, u, min(max(2 * h + 1, 0), 31));
+        uint32_t word = 0;
+        if (lane < K - 1) {
+            word = __float_as_uint(w);
+        } else if (h >= 0 && 2 * h < K) {
+            word = static_cast<uint32_t>(ua + Tp) & 0xffffu;
+            if (2 * h + 1 < K) word |= (static_cast<uint32_t>(ub + Tp) & 0xffffu) << 16;
+        }
+        if (lane < WORDS)
+            reinterpret_cast<uint32_t *>(slot + static_cast<size_t>(i) * RS)[lane] = word;
+    }
+}
+
 size_t ccm_slot_bytes(int L, int tau, int Tp) {
     size_t best = 0;
     for (int E = 1; E <= EDM_E_MAX; ++E) {
@@ -209,6 +278,30 @@ edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, int lib0, int nlib, i
     const int n_max = L - Tp;  // rows at E = 1, the most of any E
     const int RB = rows_per_cta(ctx, nlib, n_max);
     dim3 grid(nlib, (n_max + RB - 1) / RB);
+    const int ch = (L + 31) / 32;
+    if (ch <= 64) {
+        const int CHs[] = {8, 16, 24, 32, 48, 64};
+        int CH = 64;
+        for (int c : CHs)
+            if (c >= ch) { CH = c; break; }
+        const bool head1 = (EDM_E_MAX - 1) * tau < 32;
+        void (*kern)(const float *, int, int, const int32_t *, int, int, int, uint8_t *, size_t,
+                     int *) = nullptr;
+        switch (CH) {
+        case 8: kern = head1 ? ccm_table_regs_kernel<8, true> : ccm_table_regs_kernel<8, false>; break;
+        case 16: kern = head1 ? ccm_table_regs_kernel<16, true> : ccm_table_regs_kernel<16, false>; break;
+        case 24: kern = head1 ? ccm_table_regs_kernel<24, true> : ccm_table_regs_kernel<24, false>; break;
+        case 32: kern = head1 ? ccm_table_regs_kernel<32, true> : ccm_table_regs_kernel<32, false>; break;
+        case 48: kern = head1 ? ccm_table_regs_kernel<48, true> : ccm_table_regs_kernel<48, false>; break;
+        default: kern = head1 ? ccm_table_regs_kernel<64, true> : ccm_table_regs_kernel<64, false>; break;
+        }
+        const size_t smem = KNN_WARPS * sizeof(WarpScratch) + sizeof(float) * 32 * CH;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        before_launch(ctx);
+        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, lib0, L, E_lib, tau, Tp, RB, tables,
+                                                          slot_bytes, ctx->d_flags);
+        return after_launch(ctx, "ccm_table_kernel");
+    }
     const bool smem_series = sizeof(float) * static_cast<size_t>(L) <= SERIES_SMEM_MAX;
     const size_t smem = knn_smem_bytes(smem_series, L);
     if (smem_series) {

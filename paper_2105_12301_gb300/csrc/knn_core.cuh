@@ -78,10 +78,13 @@ __device__ __forceinline__ double dist64(const float *xs, int t, int u, int E, i
 }
 
 // Upper edge of the band of FP32 squared distances that may hide an FP64
-// neighbour, given the k-th smallest FP32 squared distance sK.
+// neighbour, given the k-th smallest FP32 squared distance sK:
+// sK (1 + 4 (E+3) 2^-24) + 3 * 2^-140, evaluated with upward rounding so the
+// float result is never below the exact value.  4 (E+3) 2^-24 = (E+3) 2^-22
+// is exact in float.
 __device__ __forceinline__ float band_edge(float sK, int E) {
-    double thr = static_cast<double>(sK) * (1.0 + 4.0 * (E + 3) * 0x1p-24) + 3.0 * 0x1p-140;
-    return __double2float_ru(thr);
+    const float factor = 1.0f + static_cast<float>(E + 3) * 0x1p-22f;
+    return __fadd_ru(__fmul_ru(sK, factor), 3.0f * 0x1p-140f);
 }
 
 __device__ __forceinline__ bool less64(double sa, int ua, double sb, int ub) {
@@ -291,6 +294,98 @@ __device__ int knn_row(const float *xs, int t, int lo, int hi, int tau, int K, W
     }
     __syncwarp();
     return flags;
+}
+
+// ------------------------------------------ selection from register arrays
+
+#define EDM_INF __int_as_float(0x7f800000)
+
+// Ascending bitonic sort of one float per lane; value at position r.
+__device__ __forceinline__ float warp_sorted_at_f(float v, int r) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const float o = __shfl_xor_sync(FULL, v, j);
+            const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+            v = (lower == up) ? fminf(v, o) : fmaxf(v, o);
+        }
+    }
+    return __shfl_sync(FULL, v, r);
+}
+
+// Compact the keys (s[j], lane+32j) with s[j] <= bound (and finite, i.e. a
+// candidate of P_E) into ws->key; returns
+// how many there are (only the first KNN_CAP are stored).
+template <int CH>
+__device__ __forceinline__ int compact_le(const float (&s)[CH], float bound, WarpScratch *ws) {
+    const int lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    int base = 0;
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+        const bool p = s[j] <= bound && s[j] != EDM_INF;
+        const unsigned b = __ballot_sync(FULL, p);
+        if (b) {
+            if (p) {
+                const int pos = base + __popc(b & lt);
+                if (pos < KNN_CAP) ws->key[pos] = mk_key(s[j], lane + 32 * j);
+            }
+            base += __popc(b);
+        }
+    }
+    __syncwarp();
+    return base;
+}
+
+
+// The K nearest candidates (exact FP64 neighbour set) of the query time t
+// from the FP32 squared distances held in registers: s[j] is the distance to
+// the candidate u = lane + 32 j, +inf when u is not a candidate.  Steps as in
+// knn_row's KNN_SET mode: lane minima, the (K+1)-th smallest of them as a
+// bound, ballot-compaction of the values at or below it, exact ranking of the
+// collected keys, then the band check (resolved in FP64 when it fails).  On
+// return lane r < K holds the r-th neighbour and its distance.
+template <int CH>
+__device__ __forceinline__ void select_set_regs(const float (&s)[CH], const float *xs, int t,
+                                                int lo, int hi, int E, int tau, int K,
+                                                WarpScratch *ws, int &u_out, float &d_out) {
+    const int lane = lane_id();
+    const int nc = hi - lo;
+    const int R = min(K + 1, nc);
+    float lmin = EDM_INF;
+#pragma unroll
+    for (int j = 0; j < CH; ++j) lmin = fminf(lmin, s[j]);
+    const float theta = warp_sorted_at_f(lmin, R - 1);
+    int c = compact_le<CH>(s, theta, ws);
+    if (c <= KNN_CAP) {
+        rank_keys(ws, c, R);
+        const float edge = band_edge(key_s(ws->sel[K - 1]), E);
+        if (R <= K || key_s(ws->sel[K]) > edge) {
+            if (lane < K) {
+                const uint64_t k = ws->sel[lane];
+                u_out = key_u(k);
+                d_out = sqrtf(key_s(k));
+            }
+            __syncwarp();
+            return;
+        }
+        // resolve the band in FP64
+        c = compact_le<CH>(s, edge, ws);
+        if (c <= KNN_CAP)
+            rank_band_fp64(xs, t, E, tau, ws, c, K);
+        else
+            brute_fp64(xs, t, lo, hi, E, tau, ws, K);
+    } else {
+        // more than KNN_CAP values tie at the bound (long runs of repeats)
+        brute_fp64(xs, t, lo, hi, E, tau, ws, K);
+    }
+    if (lane < K) {
+        u_out = ws->sel_u[lane];
+        d_out = __double2float_rn(__dsqrt_rn(ws->sel_s64[lane]));
+    }
+    __syncwarp();
 }
 
 // Simplex weights of the K neighbours held one per lane (lane r < K holds

@@ -188,14 +188,69 @@ struct Moments {
     static constexpr int N = BF16 ? 6 : 3;  // per target: sum a, sum a^2, sum a*b
 };
 
+// One table row (query time) for this lane's target(s): the prediction
+// y_last + sum_q w_q (y_q - y_last) over the K neighbour rows (the K-th
+// weight is 1 minus the others), accumulated into the prediction moments.
+template <int K, bool BF16, bool SMEM_TILE>
+__device__ __forceinline__ void lookup_row(const uint8_t *row, const uint32_t *tl, int yrow,
+                                           float (&m)[Moments<BF16>::N]) {
+    constexpr int RS = table_row_bytes(K);
+    constexpr int NV = RS / 16;
+    uint32_t wd[4 * NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        const uint4 v = reinterpret_cast<const uint4 *>(row)[q];
+        wd[4 * q + 0] = v.x;
+        wd[4 * q + 1] = v.y;
+        wd[4 * q + 2] = v.z;
+        wd[4 * q + 3] = v.w;
+    }
+    uint32_t g[K];  // gathered words
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        const uint32_t hw = wd[K - 1 + (q >> 1)];
+        const uint32_t u = (q & 1) ? (hw >> 16) : (hw & 0xffffu);
+        g[q] = SMEM_TILE ? tl[u * 32] : __ldg(tl + u * 32);
+    }
+    const uint32_t yv = SMEM_TILE ? tl[yrow * 32] : __ldg(tl + yrow * 32);
+    if (!BF16) {
+        const float yl = __uint_as_float(g[K - 1]);
+        float acc = yl;
+#pragma unroll
+        for (int q = 0; q < K - 1; ++q)
+            acc = __fmaf_rn(__uint_as_float(wd[q]), __fsub_rn(__uint_as_float(g[q]), yl), acc);
+        const float y = __uint_as_float(yv);
+        m[0] += acc;
+        m[1] = __fmaf_rn(acc, acc, m[1]);
+        m[2] = __fmaf_rn(acc, y, m[2]);
+    } else {
+        const float yl0 = __uint_as_float(g[K - 1] << 16);
+        const float yl1 = __uint_as_float(g[K - 1] & 0xffff0000u);
+        float acc0 = yl0, acc1 = yl1;
+#pragma unroll
+        for (int q = 0; q < K - 1; ++q) {
+            const float w = __uint_as_float(wd[q]);
+            acc0 = __fmaf_rn(w, __fsub_rn(__uint_as_float(g[q] << 16), yl0), acc0);
+            acc1 = __fmaf_rn(w, __fsub_rn(__uint_as_float(g[q] & 0xffff0000u), yl1), acc1);
+        }
+        const float y0 = __uint_as_float(yv << 16), y1 = __uint_as_float(yv & 0xffff0000u);
+        m[0] += acc0;
+        m[1] = __fmaf_rn(acc0, acc0, m[1]);
+        m[2] = __fmaf_rn(acc0, y0, m[2]);
+        m[3] += acc1;
+        m[4] = __fmaf_rn(acc1, acc1, m[4]);
+        m[5] = __fmaf_rn(acc1, y1, m[5]);
+    }
+}
+
 // Gather + accumulate one library whose k = K is a compile-time value.
+// Warps take rows warp, warp + LK_NC, ... of each chunk, two per iteration.
 template <int K, bool BF16, bool SMEM_TILE>
 __device__ __forceinline__ void consume_library(const LookupArgs &a, const uint8_t *tile,
                                                 const uint8_t *stages, uint64_t *full,
                                                 uint64_t *empty, int &seq, int n, int t0,
                                                 float (&m)[Moments<BF16>::N]) {
     constexpr int RS = table_row_bytes(K);
-    constexpr int NV = RS / 16;          // 16-byte reads per row
     constexpr int CR = LK_STAGE_BYTES / RS;
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const uint32_t *tl = reinterpret_cast<const uint32_t *>(tile) + lane;
@@ -205,57 +260,13 @@ __device__ __forceinline__ void consume_library(const LookupArgs &a, const uint8
         mbar_wait_bounded(&full[s], par, a.flags);
         const uint8_t *st = stages + static_cast<size_t>(s) * LK_STAGE_BYTES;
         const int rows = min(CR, n - c0);
-        for (int r = warp; r < rows; r += LK_NC) {
-            uint32_t wd[4 * NV];
-#pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                const uint4 v = reinterpret_cast<const uint4 *>(st + r * RS)[q];
-                wd[4 * q + 0] = v.x;
-                wd[4 * q + 1] = v.y;
-                wd[4 * q + 2] = v.z;
-                wd[4 * q + 3] = v.w;
-            }
-            float wl = 1.f;  // weight of the last neighbour: 1 - sum of the others
-#pragma unroll
-            for (int q = 0; q < K - 1; ++q) wl -= __uint_as_float(wd[q]);
-            const int yrow = t0 + c0 + r + a.Tp;
-            if (!BF16) {
-                float acc = 0.f;
-#pragma unroll
-                for (int q = 0; q < K; ++q) {
-                    const uint32_t hw = wd[K - 1 + (q >> 1)];
-                    const uint32_t u = (q & 1) ? (hw >> 16) : (hw & 0xffffu);
-                    const float v = SMEM_TILE ? __uint_as_float(tl[u * 32])
-                                              : __uint_as_float(__ldg(tl + u * 32));
-                    const float w = (q < K - 1) ? __uint_as_float(wd[q]) : wl;
-                    acc = __fmaf_rn(w, v, acc);
-                }
-                const float y = SMEM_TILE ? __uint_as_float(tl[yrow * 32])
-                                          : __uint_as_float(__ldg(tl + yrow * 32));
-                m[0] += acc;
-                m[1] = __fmaf_rn(acc, acc, m[1]);
-                m[2] = __fmaf_rn(acc, y, m[2]);
-            } else {
-                float acc0 = 0.f, acc1 = 0.f;
-#pragma unroll
-                for (int q = 0; q < K; ++q) {
-                    const uint32_t hw = wd[K - 1 + (q >> 1)];
-                    const uint32_t u = (q & 1) ? (hw >> 16) : (hw & 0xffffu);
-                    const uint32_t v = SMEM_TILE ? tl[u * 32] : __ldg(tl + u * 32);
-                    const float w = (q < K - 1) ? __uint_as_float(wd[q]) : wl;
-                    acc0 = __fmaf_rn(w, __uint_as_float(v << 16), acc0);
-                    acc1 = __fmaf_rn(w, __uint_as_float(v & 0xffff0000u), acc1);
-                }
-                const uint32_t yv = SMEM_TILE ? tl[yrow * 32] : __ldg(tl + yrow * 32);
-                const float y0 = __uint_as_float(yv << 16), y1 = __uint_as_float(yv & 0xffff0000u);
-                m[0] += acc0;
-                m[1] = __fmaf_rn(acc0, acc0, m[1]);
-                m[2] = __fmaf_rn(acc0, y0, m[2]);
-                m[3] += acc1;
-                m[4] = __fmaf_rn(acc1, acc1, m[4]);
-                m[5] = __fmaf_rn(acc1, y1, m[5]);
-            }
+        const int ybase = t0 + c0 + a.Tp;
+        int r = warp;
+        for (; r + LK_NC < rows; r += 2 * LK_NC) {
+            lookup_row<K, BF16, SMEM_TILE>(st + r * RS, tl, ybase + r, m);
+            lookup_row<K, BF16, SMEM_TILE>(st + (r + LK_NC) * RS, tl, ybase + r + LK_NC, m);
         }
+        if (r < rows) lookup_row<K, BF16, SMEM_TILE>(st + r * RS, tl, ybase + r, m);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         ++seq;

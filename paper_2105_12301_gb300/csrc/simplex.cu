@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(SX_WARPS * 32)
 }
 
 // ---------------------------------------------------------------------------
-// Incremental sweep over E (series of up to 32*CH points).
+// Incremental sweep over E (series of up to 32*CH points).  The selection from
+// registers (select_set_regs) is shared with the neighbour-table builder.
 //
 // A warp owns one query time t and keeps the FP32 squared distance from x(t)
 // to every candidate u = lane + 32 j in registers.  Going from E-1 to E adds
@@ -114,48 +115,7 @@ __global__ void __launch_bounds__(SX_WARPS * 32)
 // the warp buffer, exact ranking of the few collected keys, and the FP64
 // band check of knn_row's KNN_SET mode.
 
-#define SX_INF __int_as_float(0x7f800000)
-
-// Ascending bitonic sort of one float per lane; value at position r.
-__device__ __forceinline__ float warp_sorted_at_f(float v, int r) {
-    const int lane = lane_id();
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            const float o = __shfl_xor_sync(FULL, v, j);
-            const bool up = (lane & k) == 0, lower = (lane & j) == 0;
-            v = (lower == up) ? fminf(v, o) : fmaxf(v, o);
-        }
-    }
-    return __shfl_sync(FULL, v, r);
-}
-
-// Compact the keys (s[j], lane+32j) with s[j] <= bound (and finite, i.e. a
-// candidate of P_E) into ws->key; returns
-// how many there are (only the first KNN_CAP are stored).
-template <int CH>
-__device__ __forceinline__ int compact_le(const float (&s)[CH], float bound, WarpScratch *ws) {
-    const int lane = lane_id();
-    const unsigned lt = (1u << lane) - 1u;
-    int base = 0;
-#pragma unroll
-    for (int j = 0; j < CH; ++j) {
-        const bool p = s[j] <= bound && s[j] != SX_INF;
-        const unsigned b = __ballot_sync(FULL, p);
-        if (b) {
-            if (p) {
-                const int pos = base + __popc(b & lt);
-                if (pos < KNN_CAP) ws->key[pos] = mk_key(s[j], lane + 32 * j);
-            }
-            base += __popc(b);
-        }
-    }
-    __syncwarp();
-    return base;
-}
-
-template <int CH>
+template <int CH, bool HEAD1>
 __device__ __forceinline__ void sweep_row(const float *xs, int t, int hi, int E_max, int tau,
                                           int Tp, float mu, WarpScratch *ws, float (&m)[5]) {
     const int lane = lane_id();
@@ -163,65 +123,30 @@ __device__ __forceinline__ void sweep_row(const float *xs, int t, int hi, int E_
 #pragma unroll
     for (int j = 0; j < CH; ++j) {
         const int u = lane + 32 * j;
-        s[j] = (u <= hi && u != t) ? 0.f : SX_INF;
+        s[j] = (u <= hi && u != t) ? 0.f : EDM_INF;
     }
     for (int E = 1; E <= E_max; ++E) {
         const int lo = (E - 1) * tau;
         if (t < lo || hi - lo + 1 < E + 2) break;
         const int K = E + 1;
-        // extend every distance by the lag E-1
+        // extend every distance by the lag E-1; candidates below lo leave P_E
+        // (HEAD1: lo < 32, so only slot 0 can hold them)
         const float qv = xs[t - lo];
 #pragma unroll
         for (int j = 0; j < CH; ++j) {
             const int u = lane + 32 * j;
-            const float d = __fsub_rn(qv, xs[max(u - lo, 0)]);
-            const float v = __fmaf_rn(d, d, s[j]);
-            s[j] = (u < lo) ? SX_INF : v;
+            if (!HEAD1 || j == 0) {
+                const float d = __fsub_rn(qv, xs[max(u - lo, 0)]);
+                const float v = __fmaf_rn(d, d, s[j]);
+                s[j] = (u < lo) ? EDM_INF : v;
+            } else {
+                const float d = __fsub_rn(qv, xs[u - lo]);
+                s[j] = __fmaf_rn(d, d, s[j]);
+            }
         }
-        const int nc = hi - lo;
-        const int R = min(K + 1, nc);
-        float lmin = SX_INF;
-#pragma unroll
-        for (int j = 0; j < CH; ++j) lmin = fminf(lmin, s[j]);
-        const float theta = warp_sorted_at_f(lmin, R - 1);
-        int c = compact_le<CH>(s, theta, ws);
         int u_out = 0;
         float d_out = 0.f;
-        bool done = false;
-        if (c <= KNN_CAP) {
-            rank_keys(ws, c, R);
-            const float edge = band_edge(key_s(ws->sel[K - 1]), E);
-            if (R <= K || key_s(ws->sel[K]) > edge) {
-                if (lane < K) {
-                    const uint64_t k = ws->sel[lane];
-                    u_out = key_u(k);
-                    d_out = sqrtf(key_s(k));
-                }
-                done = true;
-            } else {
-                // resolve the band in FP64
-                c = compact_le<CH>(s, edge, ws);
-                if (c <= KNN_CAP) {
-                    rank_band_fp64(xs, t, E, tau, ws, c, K);
-                } else {
-                    brute_fp64(xs, t, lo, hi, E, tau, ws, K);
-                }
-                if (lane < K) {
-                    u_out = ws->sel_u[lane];
-                    d_out = __double2float_rn(__dsqrt_rn(ws->sel_s64[lane]));
-                }
-                done = true;
-            }
-        }
-        if (!done) {
-            // more than KNN_CAP values tie at the bound (long runs of repeats)
-            brute_fp64(xs, t, lo, hi, E, tau, ws, K);
-            if (lane < K) {
-                u_out = ws->sel_u[lane];
-                d_out = __double2float_rn(__dsqrt_rn(ws->sel_s64[lane]));
-            }
-        }
-        __syncwarp();
+        select_set_regs<CH>(s, xs, t, lo, hi, E, tau, K, ws, u_out, d_out);
         const float w = simplex_weight(d_out, K);
         const float part = lane < K ? w * __fsub_rn(xs[u_out + Tp], mu) : 0.f;
         const float a = warp_sum(part);
@@ -238,7 +163,7 @@ __device__ __forceinline__ void sweep_row(const float *xs, int t, int hi, int E_
 
 // One CTA per series (series staged in shared memory, zero-padded to 32*CH
 // points); warps take query times t = warp, warp + SX_WARPS, ...
-template <int CH>
+template <int CH, bool HEAD1>
 __global__ void __launch_bounds__(SX_WARPS * 32)
     sweep_kernel(const float *__restrict__ X, int L, int E_max, int tau, int Tp, int TB, int nrb,
                  double *__restrict__ partial) {
@@ -263,7 +188,7 @@ __global__ void __launch_bounds__(SX_WARPS * 32)
     WarpScratch *ws = wsa + warp;
     const int hi = L - 1 - Tp;
     const int t1 = min(hi + 1, (rb + 1) * TB);
-    for (int t = rb * TB + warp; t < t1; t += SX_WARPS) sweep_row<CH>(xs, t, hi, E_max, tau, Tp, mu, ws, m);
+    for (int t = rb * TB + warp; t < t1; t += SX_WARPS) sweep_row<CH, HEAD1>(xs, t, hi, E_max, tau, Tp, mu, ws, m);
 #pragma unroll
     for (int j = 0; j < 5; ++j) red[(warp * 32 + lane) * 5 + j] = m[j];
     __syncthreads();
@@ -338,13 +263,14 @@ edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max,
             if (c >= ch) { CH = c; break; }
         const size_t smem = fixed + sizeof(float) * 32 * CH;
         void (*kern)(const float *, int, int, int, int, int, int, double *) = nullptr;
+        const bool head1 = (E_max - 1) * tau < 32;
         switch (CH) {
-        case 8: kern = sweep_kernel<8>; break;
-        case 16: kern = sweep_kernel<16>; break;
-        case 24: kern = sweep_kernel<24>; break;
-        case 32: kern = sweep_kernel<32>; break;
-        case 48: kern = sweep_kernel<48>; break;
-        default: kern = sweep_kernel<64>; break;
+        case 8: kern = head1 ? sweep_kernel<8, true> : sweep_kernel<8, false>; break;
+        case 16: kern = head1 ? sweep_kernel<16, true> : sweep_kernel<16, false>; break;
+        case 24: kern = head1 ? sweep_kernel<24, true> : sweep_kernel<24, false>; break;
+        case 32: kern = head1 ? sweep_kernel<32, true> : sweep_kernel<32, false>; break;
+        case 48: kern = head1 ? sweep_kernel<48, true> : sweep_kernel<48, false>; break;
+        default: kern = head1 ? sweep_kernel<64, true> : sweep_kernel<64, false>; break;
         }
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         before_launch(ctx);

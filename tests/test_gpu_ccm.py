@@ -157,3 +157,14 @@ def test_full_size_calcium_workload_sampled():
     edm.edm_ctx_sync()
     err = np.max(np.abs(rho[rows].cpu().numpy() - ref))
     assert err <= TOL_BF16, err
+
+
+@pytest.mark.parametrize("L,tau", [(2048, 1), (2049, 1), (1000, 2), (700, 3)])
+def test_register_path_boundaries(L, tau):
+    # 2048 points: 64 candidate slots per lane (largest register path);
+    # 2049: the generic path; tau > 1 with lag offsets beyond one slot
+    X = inputs.coupled_logistic(6, L, 40 + L + tau)
+    E = check_optimal_E(X[:3], 6, tau, 1)
+    E_lib = np.array([2, 5, 1, 3, 4, 6], np.int32)
+    E_lib[:3] = E
+    check_ccm(X, X, E_lib, tau, 0, "fp32", TOL_FP32, lib_rows=[0, 4])
