@@ -22,10 +22,14 @@
 
 namespace edm {
 
-constexpr int LK_NC = 16;                      // consumer warps
-constexpr int LK_PRODUCER = LK_NC;             // warp issuing the bulk copies
-constexpr int LK_FINISHER = LK_NC + 1;         // warp turning moments into rho
-constexpr int LK_THREADS = (LK_NC + 2) * 32;
+// consumer warps: 24 with FP32 targets, 16 with BF16 (whose six moments
+// per lane need a larger hand-over buffer next to the tile)
+template <bool BF16> struct LkWarps {
+    static constexpr int NC = BF16 ? 16 : 24;
+    static constexpr int PRODUCER = NC;       // warp issuing the bulk copies
+    static constexpr int FINISHER = NC + 1;   // warp turning moments into rho
+    static constexpr int THREADS = (NC + 2) * 32;
+};
 constexpr int LK_STAGE_BYTES = 6144;           // table bytes per pipeline stage
 constexpr int LK_MAX_STAGES = 8;
 constexpr int LK_TILE_ROW = 128;               // bytes per time row of a tile
@@ -197,13 +201,20 @@ __device__ __forceinline__ void lookup_row(const uint8_t *row, const uint32_t *t
     constexpr int RS = table_row_bytes(K);
     constexpr int NV = RS / 16;
     uint32_t wd[4 * NV];
+    if (K == 2) {
+        // one weight and two 16-bit rows: 8 bytes, one 64-bit broadcast read
+        const uint2 v = *reinterpret_cast<const uint2 *>(row);
+        wd[0] = v.x;
+        wd[1] = v.y;
+    } else {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        const uint4 v = reinterpret_cast<const uint4 *>(row)[q];
-        wd[4 * q + 0] = v.x;
-        wd[4 * q + 1] = v.y;
-        wd[4 * q + 2] = v.z;
-        wd[4 * q + 3] = v.w;
+        for (int q = 0; q < NV; ++q) {
+            const uint4 v = reinterpret_cast<const uint4 *>(row)[q];
+            wd[4 * q + 0] = v.x;
+            wd[4 * q + 1] = v.y;
+            wd[4 * q + 2] = v.z;
+            wd[4 * q + 3] = v.w;
+        }
     }
     uint32_t g[K];  // gathered words
 #pragma unroll
@@ -252,6 +263,7 @@ __device__ __forceinline__ void consume_library(const LookupArgs &a, const uint8
                                                 float (&m)[Moments<BF16>::N]) {
     constexpr int RS = table_row_bytes(K);
     constexpr int CR = LK_STAGE_BYTES / RS;
+    constexpr int LK_NC = LkWarps<BF16>::NC;
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const uint32_t *tl = reinterpret_cast<const uint32_t *>(tile) + lane;
     for (int c0 = 0; c0 < n; c0 += CR) {
@@ -281,9 +293,12 @@ __device__ __forceinline__ float finish_rho(double n, double sa, double saa, dou
 }
 
 template <bool BF16, bool SMEM_TILE>
-__global__ void __launch_bounds__(LK_THREADS, 1) lookup_kernel(const LookupArgs a) {
+__global__ void __launch_bounds__(LkWarps<BF16>::THREADS, 1) lookup_kernel(const LookupArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     constexpr int NM = Moments<BF16>::N;
+    constexpr int LK_NC = LkWarps<BF16>::NC;
+    constexpr int LK_PRODUCER = LkWarps<BF16>::PRODUCER;
+    constexpr int LK_FINISHER = LkWarps<BF16>::FINISHER;
     constexpr int TT = BF16 ? 64 : 32;
     const int tile_id = blockIdx.x;
     const int lb0 = a.lib0 + blockIdx.y * a.LB;
@@ -429,6 +444,8 @@ edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, cons
     const int tt = targets_per_tile(prec);
     const int n_tiles = (N_tgt + tt - 1) / tt;
     const int nm = bf16 ? 6 : 3;
+    const int LK_NC = bf16 ? LkWarps<true>::NC : LkWarps<false>::NC;
+    const int threads = bf16 ? LkWarps<true>::THREADS : LkWarps<false>::THREADS;
     const size_t tile_bytes = static_cast<size_t>(L) * LK_TILE_ROW;
     const size_t fixed = static_cast<size_t>(2) * LK_NC * nm * 32 * sizeof(float) +
                          (2 * LK_MAX_STAGES + 5) * sizeof(uint64_t);
@@ -473,7 +490,7 @@ edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, cons
         kern = smem_tile ? lookup_kernel<false, true> : lookup_kernel<false, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     before_launch(ctx);
-    kern<<<grid, LK_THREADS, smem, ctx->stream>>>(a);
+    kern<<<grid, threads, smem, ctx->stream>>>(a);
     return after_launch(ctx, "lookup_kernel");
 }
 
