@@ -138,6 +138,33 @@ edm_status edm_simplex_optimal_E(edm_ctx *ctx, const float *X, int N, int L,
                                  int E_max, int tau, int Tp_sel,
                                  int32_t *E_opt, float *rho_E);
 
+/* edm_simplex_optimal_E for callers that must not allocate device memory.
+ * The paper has no counterpart; this is a deployment variant.  It is meant
+ * for code that may not call cudaMalloc once it is running: a latency-bound
+ * streaming pipeline (cudaMalloc can synchronise the whole device and takes
+ * unbounded time), a plug-in inside a host application or framework whose
+ * own allocator owns the GPU's memory, or a service that reserves all device
+ * memory at start-up.  It takes no context and allocates nothing: the
+ * caller passes inputs and outputs (device pointers, as for
+ * edm_simplex_optimal_E) and a stream (cudaStream_t; NULL = legacy default).
+ * Its only scratch memory, the partial Pearson moments, is a fixed array of
+ * 2^19 doubles (4 MiB) compiled into the library, which every GPU that loads
+ * the library keeps until the process exits.  Capacity: N * E_max must not
+ * exceed 104,857 (for example N <= 5,242 series at E_max = 20); larger
+ * requests return EDM_ERR_INVALID_ARG before anything is enqueued.
+ * The first call on a device looks up the array's device address (with that
+ * device current), so make that first call before any stream capture.
+ * Every call shares the one array: the sweep kernel rewrites every entry the
+ * finishing kernel reads, so nothing stale is used, but two calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race
+ * and both results are then undefined.  Serialise them.
+ * Results equal those of edm_simplex_optimal_E on the same inputs.  Errors
+ * are returned only as status codes (there is no context to hold a message);
+ * launch failures return EDM_ERR_CUDA. */
+edm_status edm_simplex_optimal_E_noalloc(const float *X, int N, int L, int E_max,
+                                         int tau, int Tp_sel, int32_t *E_opt,
+                                         float *rho_E, void *cuda_stream);
+
 /* Section 2.1 steps 1-4 for every (library, target) pair (pairwise CCM,
  * section 3.3 "Lookup").  X_lib [N_lib][L], Y_tgt [N_tgt][L] float32 (they
  * may be the same array).  E_lib [N_lib] int32 on the device: the embedding

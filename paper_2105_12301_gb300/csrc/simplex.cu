@@ -11,6 +11,8 @@
 // the weighted prediction.  Prediction and observation are centred on the
 // series mean before their moments are accumulated (FP32 per warp, FP64
 // across warps and CTAs); rho is finished in FP64 by a second kernel.
+#include <mutex>
+
 #include "knn_core.cuh"
 
 namespace edm {
@@ -300,4 +302,102 @@ edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max,
     return after_launch(ctx, "simplex_finish_kernel");
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of edm_simplex_optimal_E (no counterpart in the
+// paper).  Its only scratch memory -- the per-CTA partial moments that the
+// sweep kernels write and the finishing kernel reads -- lives in the
+// file-scope array below instead of a context workspace.  Every GPU that
+// loads the library holds this array until the process exits.
+
+constexpr size_t NOALLOC_SCRATCH_DOUBLES = size_t(1) << 19;  // 4 MiB
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
+
+// Device address of g_noalloc_scratch on each device, looked up once per
+// device (with that device current) on the first call there.
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static double *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mutex;
+
+static cudaError_t noalloc_scratch(int device, double **ptr) {
+    if (device < 0 || device >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[device] = static_cast<double *>(p);
+    }
+    *ptr = g_noalloc_ptr[device];
+    return cudaSuccess;
+}
+
 }  // namespace edm
+
+extern "C" edm_status edm_simplex_optimal_E_noalloc(const float *X, int N, int L, int E_max,
+                                                    int tau, int Tp_sel, int32_t *E_opt,
+                                                    float *rho_E, void *cuda_stream) {
+    using namespace edm;
+    if (!X || !E_opt || N < 1 || L < 2 || L > EDM_L_MAX || E_max < 1 || E_max > EDM_E_MAX ||
+        tau < 1 || Tp_sel < 0 || L - Tp_sel < 3)
+        return EDM_ERR_INVALID_ARG;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    int device = 0, num_sms = 0;
+    if (cudaGetDevice(&device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return EDM_ERR_CUDA;
+    // query times per CTA: the same split as the context path, widened until
+    // the partial moments fit the static scratch
+    const long long want_ctas = 8LL * num_sms;
+    const long long per_series = (want_ctas + N - 1) / N;
+    int TB = static_cast<int>((L + per_series - 1) / per_series);
+    TB = std::min(std::max(TB, 4 * SX_WARPS), L);
+    int nrb = (L + TB - 1) / TB;
+    const size_t per_block = static_cast<size_t>(E_max) * 5;
+    if (static_cast<size_t>(N) * nrb * per_block > NOALLOC_SCRATCH_DOUBLES) {
+        TB = L;
+        nrb = 1;
+    }
+    if (static_cast<size_t>(N) * nrb * per_block > NOALLOC_SCRATCH_DOUBLES)
+        return EDM_ERR_INVALID_ARG;  // N * E_max above the scratch capacity
+    double *partial = nullptr;
+    if (noalloc_scratch(device, &partial) != cudaSuccess) return EDM_ERR_CUDA;
+
+    const size_t fixed = SX_WARPS * sizeof(WarpScratch) + SX_WARPS * 32 * 5 * sizeof(float) +
+                         SX_WARPS * sizeof(double);
+    dim3 grid(N, nrb);
+    const int ch = (L + 31) / 32;
+    if (ch <= 64) {
+        const int CHs[] = {8, 16, 24, 32, 48, 64};
+        int CH = 64;
+        for (int c : CHs)
+            if (c >= ch) { CH = c; break; }
+        const size_t smem = fixed + sizeof(float) * 32 * CH;
+        const bool head1 = (E_max - 1) * tau < 32;
+        void (*kern)(const float *, int, int, int, int, int, int, double *) = nullptr;
+        switch (CH) {
+        case 8: kern = head1 ? sweep_kernel<8, true> : sweep_kernel<8, false>; break;
+        case 16: kern = head1 ? sweep_kernel<16, true> : sweep_kernel<16, false>; break;
+        case 24: kern = head1 ? sweep_kernel<24, true> : sweep_kernel<24, false>; break;
+        case 32: kern = head1 ? sweep_kernel<32, true> : sweep_kernel<32, false>; break;
+        case 48: kern = head1 ? sweep_kernel<48, true> : sweep_kernel<48, false>; break;
+        default: kern = head1 ? sweep_kernel<64, true> : sweep_kernel<64, false>; break;
+        }
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return EDM_ERR_CUDA;
+        kern<<<grid, SX_WARPS * 32, smem, stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial);
+    } else {
+        const bool smem_series = sizeof(float) * static_cast<size_t>(L) <= SX_SERIES_SMEM_MAX;
+        const size_t smem = fixed + (smem_series ? align_up(sizeof(float) * L, 16) : 0);
+        auto kern = smem_series ? simplex_kernel<true> : simplex_kernel<false>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return EDM_ERR_CUDA;
+        kern<<<grid, SX_WARPS * 32, smem, stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial);
+    }
+    if (cudaGetLastError() != cudaSuccess) return EDM_ERR_CUDA;
+    simplex_finish_kernel<<<(N + 127) / 128, 128, 0, stream>>>(partial, N, L, E_max, tau, Tp_sel,
+                                                                nrb, E_opt, rho_E);
+    if (cudaGetLastError() != cudaSuccess) return EDM_ERR_CUDA;
+    return EDM_OK;
+}

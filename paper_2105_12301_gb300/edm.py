@@ -71,6 +71,7 @@ def load():
     lib.edm_simplex_optimal_E.argtypes = [vp, vp, ci, ci, ci, ci, ci, vp, vp]
     lib.edm_ccm_all.argtypes = [vp, vp, ci, vp, ci, ci, vp, ci, ci, ci, vp]
     lib.edm_ccm_batched.argtypes = [vp, ctypes.POINTER(edm_instance), ci, ci]
+    lib.edm_simplex_optimal_E_noalloc.argtypes = [vp, ci, ci, ci, ci, ci, vp, vp, vp]
     lib.edm_profile_enable.argtypes = [vp, ci]
     lib.edm_profile_read.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ci)]
@@ -78,7 +79,8 @@ def load():
                                              ctypes.POINTER(ctypes.c_double)]
     for f in ("edm_create", "edm_destroy", "edm_set_stream", "edm_ctx_sync", "edm_embed",
               "edm_knn", "edm_simplex_optimal_E", "edm_ccm_all", "edm_ccm_batched",
-              "edm_profile_enable", "edm_profile_read", "edm_probe_smem_bandwidth"):
+              "edm_profile_enable", "edm_profile_read", "edm_probe_smem_bandwidth",
+              "edm_simplex_optimal_E_noalloc"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -195,6 +197,27 @@ def edm_simplex_optimal_E(X, E_max=EDM_E_MAX, tau=1, Tp_sel=1, with_rho=True):
     ctx = _ctx(X.device)
     _check(ctx, load().edm_simplex_optimal_E(ctx, _ptr(X), N, L, E_max, tau, Tp_sel,
                                              _ptr(E_opt), _ptr(rho_E)), "edm_simplex_optimal_E")
+    return E_opt, rho_E
+
+
+def edm_simplex_optimal_E_noalloc(X, E_opt, rho_E=None, E_max=EDM_E_MAX, tau=1, Tp_sel=1):
+    """Optimal E into caller-allocated outputs, with no device allocation in
+    the library (for callers that may not allocate once running; see
+    include/edm.h).  E_opt: CUDA int32 [N]; rho_E: CUDA float32 [N][E_max]
+    or None.  Runs on torch's current stream of X's device."""
+    _series(X, "X", 2)
+    N, L = X.shape
+    if E_opt.dtype != torch.int32 or E_opt.shape != (N,) or not E_opt.is_cuda:
+        raise TypeError("E_opt must be a CUDA int32 tensor of shape [N]")
+    if rho_E is not None and (rho_E.dtype != torch.float32 or rho_E.shape != (N, E_max)
+                              or not rho_E.is_contiguous()):
+        raise TypeError("rho_E must be a contiguous CUDA float32 tensor of shape [N][E_max]")
+    stream = torch.cuda.current_stream(X.device).cuda_stream
+    with torch.cuda.device(X.device):
+        st = load().edm_simplex_optimal_E_noalloc(_ptr(X), N, L, E_max, tau, Tp_sel, _ptr(E_opt),
+                                                  _ptr(rho_E), ctypes.c_void_p(stream))
+    if st != EDM_OK:
+        raise EdmError(st, "edm_simplex_optimal_E_noalloc(N=%d, L=%d, E_max=%d)" % (N, L, E_max))
     return E_opt, rho_E
 
 
