@@ -53,10 +53,19 @@ edm_status after_launch(edm_ctx *ctx, const char *kernel);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Layout of one row of a CCM neighbour table (k = E+1 neighbours): the
-// first k-1 normalised weights as float32 (the k-th is 1 minus their sum),
-// then the k neighbour rows (time index + Tp) as uint16, padded to 16 bytes.
-__host__ __device__ constexpr int table_row_bytes(int k) { return ((4 * (k - 1) + 2 * k + 15) / 16) * 16; }
+// Layout of a CCM neighbour table (k = E+1 neighbours, n rows).  Rows are
+// stored in pairs (2p, 2p+1).  A row's logical words are its first k-1
+// normalised weights (float32; the k-th is 1 minus their sum) followed by
+// its k neighbour rows (time index + Tp) packed two per 32-bit word (low half
+// first).  In a pair block, logical word j of row 2p sits at word 2j and that
+// of row 2p+1 at word 2j+1, so one 16-byte read gives both rows' values as
+// register pairs.  Blocks are padded to 16 bytes.  When n is odd the last
+// block's second row is a dummy: weights 0 and every neighbour row equal to
+// L, the all-zero time row that every target tile carries after its L rows.
+__host__ __device__ constexpr int table_row_words(int k) { return (k - 1) + (k + 1) / 2; }
+__host__ __device__ constexpr int table_pair_bytes(int k) {
+    return ((8 * table_row_words(k) + 15) / 16) * 16;
+}
 
 // Launchers (one translation unit each).
 edm_status launch_embed(edm_ctx *ctx, const float *x, int L, int E, int tau, float *out);

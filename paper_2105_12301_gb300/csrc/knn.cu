@@ -126,34 +126,44 @@ edm_status launch_knn(edm_ctx *ctx, const float *X, int N, int L, int E, int tau
 
 // ----------------------------------------------------- CCM neighbour tables
 
+// Write row i of a library's table (pair-interleaved layout, see
+// table_pair_bytes).  Lane r < K holds neighbour r (time index u) and its
+// normalised weight w.  The warp that writes the last row of an odd table
+// also writes the dummy row that completes its pair.
+__device__ __forceinline__ void write_table_row(uint8_t *slot, int i, int n, int K, int L, int Tp,
+                                                int u, float w) {
+    const int lane = lane_id();
+    const int words = table_row_words(K);
+    const int h = lane - (K - 1);
+    const int ua = __shfl_sync(FULL, u, min(max(2 * h, 0), 31));
+    const int ub = __shfl_sync(FULL, u, min(max(2 * h + 1, 0), 31));
+    uint32_t word = 0;
+    if (lane < K - 1) {
+        word = __float_as_uint(w);
+    } else if (h >= 0 && 2 * h < K) {
+        word = static_cast<uint32_t>(ua + Tp) & 0xffffu;
+        if (2 * h + 1 < K) word |= (static_cast<uint32_t>(ub + Tp) & 0xffffu) << 16;
+    }
+    uint32_t *block = reinterpret_cast<uint32_t *>(slot + static_cast<size_t>(i >> 1) * table_pair_bytes(K));
+    if (lane < words) block[2 * lane + (i & 1)] = word;
+    if ((n & 1) && i == n - 1 && lane < words)
+        block[2 * lane + 1] = lane < K - 1 ? 0u : (static_cast<uint32_t>(L) | (static_cast<uint32_t>(L) << 16));
+}
+
 // Rows [r0, r1) of one library's table: the exact FP64 neighbour set,
 // normalised simplex weights, neighbour rows pre-shifted by Tp.
 template <int E>
 __device__ __forceinline__ void table_rows(const float *xs, int L, int tau, int Tp, int r0, int r1,
                                            WarpScratch *ws, uint8_t *slot) {
     constexpr int K = E + 1;
-    constexpr int RS = table_row_bytes(K);
-    constexpr int WORDS = RS / 4;
-    const int lo = (E - 1) * tau, hi = L - 1 - Tp;
-    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const int lo = (E - 1) * tau, hi = L - 1 - Tp, n = hi - lo + 1;
+    const int warp = threadIdx.x >> 5;
     for (int i = r0 + warp; i < r1; i += KNN_WARPS) {
         int u = 0;
         float d = 0.f;
         knn_row<E, KNN_SET>(xs, lo + i, lo, hi, tau, K, ws, &u, &d);
         const float w = simplex_weight(d, K);
-        // word j < K-1: weight j; word K-1+h: rows 2h (low half) and 2h+1 (high)
-        const int h = lane - (K - 1);
-        const int ua = __shfl_sync(FULL, u, min(max(2 * h, 0), 31));
-        const int ub = __shfl_sync(FULL, u, min(max(2 * h + 1, 0), 31));
-        uint32_t word = 0;
-        if (lane < K - 1) {
-            word = __float_as_uint(w);
-        } else if (h >= 0 && 2 * h < K) {
-            word = static_cast<uint32_t>(ua + Tp) & 0xffffu;
-            if (2 * h + 1 < K) word |= (static_cast<uint32_t>(ub + Tp) & 0xffffu) << 16;
-        }
-        if (lane < WORDS)
-            reinterpret_cast<uint32_t *>(slot + static_cast<size_t>(i) * RS)[lane] = word;
+        write_table_row(slot, i, n, K, L, Tp, u, w);
     }
 }
 
@@ -223,7 +233,6 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
     const int warp = threadIdx.x >> 5, lane = lane_id();
     WarpScratch *ws = wsa + warp;
     uint8_t *slot = tables + static_cast<size_t>(blockIdx.x) * slot_bytes;
-    const int RS = table_row_bytes(K), WORDS = RS / 4;
     for (int i = r0 + warp; i < r1; i += KNN_WARPS) {
         const int t = lo + i;
         float s[CH];
@@ -247,18 +256,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
         float d = 0.f;
         select_set_regs<CH>(s, xs, t, lo, hi, E, tau, K, ws, u, d);
         const float w = simplex_weight(d, K);
-        const int h = lane - (K - 1);
-        const int ua = __shfl_sync(FULL, u, min(max(2 * h, 0), 31));
-        const int ub = __shfl_sync(FULL, u, min(max(2 * h + 1, 0), 31));
-        uint32_t word = 0;
-        if (lane < K - 1) {
-            word = __float_as_uint(w);
-        } else if (h >= 0 && 2 * h < K) {
-            word = static_cast<uint32_t>(ua + Tp) & 0xffffu;
-            if (2 * h + 1 < K) word |= (static_cast<uint32_t>(ub + Tp) & 0xffffu) << 16;
-        }
-        if (lane < WORDS)
-            reinterpret_cast<uint32_t *>(slot + static_cast<size_t>(i) * RS)[lane] = word;
+        write_table_row(slot, i, n, K, L, Tp, u, w);
     }
 }
 
@@ -267,7 +265,7 @@ size_t ccm_slot_bytes(int L, int tau, int Tp) {
     for (int E = 1; E <= EDM_E_MAX; ++E) {
         const int n = L - (E - 1) * tau - Tp;
         if (n < 1) break;
-        best = std::max(best, static_cast<size_t>(n) * table_row_bytes(E + 1));
+        best = std::max(best, static_cast<size_t>((n + 1) / 2) * table_pair_bytes(E + 1));
     }
     return align_up(best, 256);
 }

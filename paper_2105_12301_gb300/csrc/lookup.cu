@@ -50,6 +50,8 @@ __global__ void target_mean_kernel(const float *__restrict__ Y, int N, int L,
 // FP32: Yt[tile][u][32] = Y[32 tile + lane][u] - mean; pad targets are 0.
 // BF16: Yt[tile][u][64] bf16, lane l's 32-bit word holds targets 2l (low
 // half) and 2l+1 (high half), each rounded to nearest even.
+// Every tile has L+1 time rows; row L is all zeros (the dummy neighbour row
+// of odd-length tables).
 template <bool BF16>
 __global__ void target_store_kernel(const float *__restrict__ Y, int N, int L,
                                     const double *__restrict__ mean, uint8_t *__restrict__ Yt) {
@@ -66,7 +68,9 @@ __global__ void target_store_kernel(const float *__restrict__ Y, int N, int L,
         s[j][tx] = v;
     }
     __syncthreads();
-    uint8_t *base = Yt + static_cast<size_t>(tile) * L * LK_TILE_ROW;
+    uint8_t *base = Yt + static_cast<size_t>(tile) * (L + 1) * LK_TILE_ROW;
+    if (blockIdx.y == 0 && ty == 0)
+        reinterpret_cast<uint32_t *>(base + static_cast<size_t>(L) * LK_TILE_ROW)[tx] = 0u;
     for (int r = ty; r < 32; r += 8) {
         const int u = u0 + r;
         if (u >= L) continue;
@@ -86,7 +90,7 @@ template <bool BF16>
 __device__ __forceinline__ float stored_target(const uint8_t *Yt, int L, int tgt, int u) {
     constexpr int TT = BF16 ? 64 : 32;
     const uint32_t *row = reinterpret_cast<const uint32_t *>(
-        Yt + (static_cast<size_t>(tgt / TT) * L + u) * LK_TILE_ROW);
+        Yt + (static_cast<size_t>(tgt / TT) * (L + 1) + u) * LK_TILE_ROW);
     if (!BF16) return __uint_as_float(row[tgt % 32]);
     const uint32_t v = row[(tgt % 64) >> 1];
     return __uint_as_float((tgt & 1) ? (v & 0xffff0000u) : (v << 16));
@@ -134,7 +138,7 @@ static int targets_per_tile(edm_precision prec) { return prec == EDM_BF16_TARGET
 size_t target_store_bytes(int N_tgt, int L, edm_precision prec) {
     const int tt = targets_per_tile(prec);
     const size_t tiles = (N_tgt + tt - 1) / tt;
-    return align_up(tiles * L * LK_TILE_ROW, 256);
+    return align_up(tiles * (L + 1) * LK_TILE_ROW, 256);
 }
 
 edm_status launch_target_store(edm_ctx *ctx, const float *Y, int N_tgt, int L, int tau, int Tp,
@@ -184,101 +188,99 @@ __device__ __forceinline__ bool lib_valid(int E, int L, int tau, int Tp) {
     return E >= 1 && E <= EDM_E_MAX && L - (E - 1) * tau - Tp >= E + 2;
 }
 
-// Rows of one table chunk: as many whole rows as fit a stage.
-__device__ __forceinline__ int chunk_rows(int K) { return LK_STAGE_BYTES / table_row_bytes(K); }
+// Row pairs of one table chunk: as many whole pair blocks as fit a stage.
+__host__ __device__ constexpr int chunk_pairs(int K) { return LK_STAGE_BYTES / table_pair_bytes(K); }
 
 template <bool BF16>
 struct Moments {
     static constexpr int N = BF16 ? 6 : 3;  // per target: sum a, sum a^2, sum a*b
 };
 
-// One table row (query time) for this lane's target(s): the prediction
-// y_last + sum_q w_q (y_q - y_last) over the K neighbour rows (the K-th
-// weight is 1 minus the others), accumulated into the prediction moments.
+// Per-lane prediction moments: for each of the lane's targets, the sums of
+// the prediction, of its square and of its product with the observation,
+// kept as (row 2p, row 2p+1) pairs for the packed FP32x2 arithmetic.
+template <bool BF16>
+struct PairMoments {
+    static constexpr int T = BF16 ? 2 : 1;  // targets per lane
+    float2 s[T], ss[T], sy[T];
+};
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// One table pair block (query times 2p and 2p+1) for this lane's target(s).
+// For each row the prediction is y_last + sum_q w_q (y_q - y_last) over its
+// K neighbour rows (the K-th weight is 1 minus the others); the two rows run
+// side by side in FFMA2/FADD2 lanes.  y_q - y_last is formed as
+// fma(y_last, -1, y_q): the exact difference rounded once, as a subtraction.
 template <int K, bool BF16, bool SMEM_TILE>
-__device__ __forceinline__ void lookup_row(const uint8_t *row, const uint32_t *tl, int yrow,
-                                           float (&m)[Moments<BF16>::N]) {
-    constexpr int RS = table_row_bytes(K);
-    constexpr int NV = RS / 16;
+__device__ __forceinline__ void lookup_pair(const uint8_t *blk, const uint32_t *tl, int yrow,
+                                            PairMoments<BF16> &m) {
+    constexpr int PB = table_pair_bytes(K);
+    constexpr int NV = PB / 16;
     uint32_t wd[4 * NV];
-    if (K == 2) {
-        // one weight and two 16-bit rows: 8 bytes, one 64-bit broadcast read
-        const uint2 v = *reinterpret_cast<const uint2 *>(row);
-        wd[0] = v.x;
-        wd[1] = v.y;
-    } else {
 #pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            const uint4 v = reinterpret_cast<const uint4 *>(row)[q];
-            wd[4 * q + 0] = v.x;
-            wd[4 * q + 1] = v.y;
-            wd[4 * q + 2] = v.z;
-            wd[4 * q + 3] = v.w;
-        }
+    for (int q = 0; q < NV; ++q) {
+        const uint4 v = reinterpret_cast<const uint4 *>(blk)[q];
+        wd[4 * q + 0] = v.x;
+        wd[4 * q + 1] = v.y;
+        wd[4 * q + 2] = v.z;
+        wd[4 * q + 3] = v.w;
     }
-    uint32_t g[K];  // gathered words
+    uint32_t gA[K], gB[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) {
-        const uint32_t hw = wd[K - 1 + (q >> 1)];
-        const uint32_t u = (q & 1) ? (hw >> 16) : (hw & 0xffffu);
-        g[q] = SMEM_TILE ? tl[u * 32] : __ldg(tl + u * 32);
+        const uint32_t hA = wd[2 * (K - 1 + (q >> 1))], hB = wd[2 * (K - 1 + (q >> 1)) + 1];
+        const uint32_t uA = (q & 1) ? (hA >> 16) : (hA & 0xffffu);
+        const uint32_t uB = (q & 1) ? (hB >> 16) : (hB & 0xffffu);
+        gA[q] = SMEM_TILE ? tl[uA * 32] : __ldg(tl + uA * 32);
+        gB[q] = SMEM_TILE ? tl[uB * 32] : __ldg(tl + uB * 32);
     }
-    const uint32_t yv = SMEM_TILE ? tl[yrow * 32] : __ldg(tl + yrow * 32);
-    if (!BF16) {
-        const float yl = __uint_as_float(g[K - 1]);
-        float acc = yl;
+    const uint32_t yA = SMEM_TILE ? tl[yrow * 32] : __ldg(tl + yrow * 32);
+    const uint32_t yB = SMEM_TILE ? tl[(yrow + 1) * 32] : __ldg(tl + (yrow + 1) * 32);
+    const float2 m1 = f2(-1.f, -1.f);
 #pragma unroll
-        for (int q = 0; q < K - 1; ++q)
-            acc = __fmaf_rn(__uint_as_float(wd[q]), __fsub_rn(__uint_as_float(g[q]), yl), acc);
-        const float y = __uint_as_float(yv);
-        m[0] += acc;
-        m[1] = __fmaf_rn(acc, acc, m[1]);
-        m[2] = __fmaf_rn(acc, y, m[2]);
-    } else {
-        const float yl0 = __uint_as_float(g[K - 1] << 16);
-        const float yl1 = __uint_as_float(g[K - 1] & 0xffff0000u);
-        float acc0 = yl0, acc1 = yl1;
+    for (int c = 0; c < PairMoments<BF16>::T; ++c) {
+        // c selects the lane's target: FP32 word, or BF16 low / high half
+        auto val = [&](uint32_t v) {
+            return __uint_as_float(BF16 ? (c == 0 ? (v << 16) : (v & 0xffff0000u)) : v);
+        };
+        const float2 yl = f2(val(gA[K - 1]), val(gB[K - 1]));
+        float2 acc = yl;
 #pragma unroll
         for (int q = 0; q < K - 1; ++q) {
-            const float w = __uint_as_float(wd[q]);
-            acc0 = __fmaf_rn(w, __fsub_rn(__uint_as_float(g[q] << 16), yl0), acc0);
-            acc1 = __fmaf_rn(w, __fsub_rn(__uint_as_float(g[q] & 0xffff0000u), yl1), acc1);
+            const float2 w = f2(__uint_as_float(wd[2 * q]), __uint_as_float(wd[2 * q + 1]));
+            const float2 diff = __ffma2_rn(yl, m1, f2(val(gA[q]), val(gB[q])));
+            acc = __ffma2_rn(w, diff, acc);
         }
-        const float y0 = __uint_as_float(yv << 16), y1 = __uint_as_float(yv & 0xffff0000u);
-        m[0] += acc0;
-        m[1] = __fmaf_rn(acc0, acc0, m[1]);
-        m[2] = __fmaf_rn(acc0, y0, m[2]);
-        m[3] += acc1;
-        m[4] = __fmaf_rn(acc1, acc1, m[4]);
-        m[5] = __fmaf_rn(acc1, y1, m[5]);
+        const float2 y = f2(val(yA), val(yB));
+        m.s[c] = __fadd2_rn(m.s[c], acc);
+        m.ss[c] = __ffma2_rn(acc, acc, m.ss[c]);
+        m.sy[c] = __ffma2_rn(acc, y, m.sy[c]);
     }
 }
 
 // Gather + accumulate one library whose k = K is a compile-time value.
-// Warps take rows warp, warp + LK_NC, ... of each chunk, two per iteration.
+// Warps take pair blocks warp, warp + NC, ... of each chunk.
 template <int K, bool BF16, bool SMEM_TILE>
 __device__ __forceinline__ void consume_library(const LookupArgs &a, const uint8_t *tile,
                                                 const uint8_t *stages, uint64_t *full,
                                                 uint64_t *empty, int &seq, int n, int t0,
-                                                float (&m)[Moments<BF16>::N]) {
-    constexpr int RS = table_row_bytes(K);
-    constexpr int CR = LK_STAGE_BYTES / RS;
+                                                PairMoments<BF16> &m) {
+    constexpr int PB = table_pair_bytes(K);
+    constexpr int CP = LK_STAGE_BYTES / PB;
     constexpr int LK_NC = LkWarps<BF16>::NC;
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const uint32_t *tl = reinterpret_cast<const uint32_t *>(tile) + lane;
-    for (int c0 = 0; c0 < n; c0 += CR) {
+    const int npairs = (n + 1) >> 1;
+    for (int p0 = 0; p0 < npairs; p0 += CP) {
         const int s = seq % a.stages;
         const uint32_t par = (seq / a.stages) & 1;
         mbar_wait_bounded(&full[s], par, a.flags);
         const uint8_t *st = stages + static_cast<size_t>(s) * LK_STAGE_BYTES;
-        const int rows = min(CR, n - c0);
-        const int ybase = t0 + c0 + a.Tp;
-        int r = warp;
-        for (; r + LK_NC < rows; r += 2 * LK_NC) {
-            lookup_row<K, BF16, SMEM_TILE>(st + r * RS, tl, ybase + r, m);
-            lookup_row<K, BF16, SMEM_TILE>(st + (r + LK_NC) * RS, tl, ybase + r + LK_NC, m);
-        }
-        if (r < rows) lookup_row<K, BF16, SMEM_TILE>(st + r * RS, tl, ybase + r, m);
+        const int pairs = min(CP, npairs - p0);
+        const int ybase = t0 + a.Tp + 2 * p0;
+        for (int p = warp; p < pairs; p += LK_NC)
+            lookup_pair<K, BF16, SMEM_TILE>(st + p * PB, tl, ybase + 2 * p, m);
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         ++seq;
@@ -303,7 +305,7 @@ __global__ void __launch_bounds__(LkWarps<BF16>::THREADS, 1) lookup_kernel(const
     const int tile_id = blockIdx.x;
     const int lb0 = a.lib0 + blockIdx.y * a.LB;
     const int lb1 = min(a.lib0 + a.nlib, lb0 + a.LB);
-    const size_t tile_bytes = static_cast<size_t>(a.L) * LK_TILE_ROW;
+    const size_t tile_bytes = static_cast<size_t>(a.L + 1) * LK_TILE_ROW;
     const uint8_t *tile_g = a.Yt + static_cast<size_t>(tile_id) * tile_bytes;
     uint8_t *tile_s = smem;
     uint8_t *stages = smem + (SMEM_TILE ? tile_bytes : 0);
@@ -342,16 +344,17 @@ __global__ void __launch_bounds__(LkWarps<BF16>::THREADS, 1) lookup_kernel(const
                 const int E = a.E_lib[lib];
                 if (!lib_valid(E, a.L, a.tau, a.Tp)) continue;
                 const int n = a.L - (E - 1) * a.tau - a.Tp;
-                const int RS = table_row_bytes(E + 1);
-                const int CR = chunk_rows(E + 1);
+                const int npairs = (n + 1) >> 1;
+                const int PB = table_pair_bytes(E + 1);
+                const int CP = chunk_pairs(E + 1);
                 const uint8_t *slot = a.tables + static_cast<size_t>(lib - a.lib0) * a.slot_bytes;
-                for (int c0 = 0; c0 < n; c0 += CR) {
+                for (int p0 = 0; p0 < npairs; p0 += CP) {
                     const int s = seq % a.stages, j = seq / a.stages;
                     if (j > 0) mbar_wait_bounded(&empty[s], (j - 1) & 1, a.flags);
-                    const uint32_t bytes = static_cast<uint32_t>(min(CR, n - c0) * RS);
+                    const uint32_t bytes = static_cast<uint32_t>(min(CP, npairs - p0) * PB);
                     mbar_arrive_expect_tx(&full[s], bytes);
                     bulk_copy_g2s(stages + static_cast<size_t>(s) * LK_STAGE_BYTES,
-                                  slot + static_cast<size_t>(c0) * RS, bytes, &full[s]);
+                                  slot + static_cast<size_t>(p0) * PB, bytes, &full[s]);
                     ++seq;
                 }
             }
@@ -407,16 +410,17 @@ __global__ void __launch_bounds__(LkWarps<BF16>::THREADS, 1) lookup_kernel(const
     const uint8_t *tile = SMEM_TILE ? tile_s : tile_g;
     if (SMEM_TILE) mbar_wait_bounded(tbar, 0, a.flags);
     int seq = 0, done = 0;
-    float m[NM];
+    PairMoments<BF16> pm;
     for (int lib = lb0; lib < lb1; ++lib) {
         const int E = a.E_lib[lib];
         if (!lib_valid(E, a.L, a.tau, a.Tp)) continue;
         const int n = a.L - (E - 1) * a.tau - a.Tp, t0 = (E - 1) * a.tau;
 #pragma unroll
-        for (int j = 0; j < NM; ++j) m[j] = 0.f;
+        for (int c = 0; c < PairMoments<BF16>::T; ++c)
+            pm.s[c] = pm.ss[c] = pm.sy[c] = f2(0.f, 0.f);
         switch (E + 1) {
 #define EDM_CASE(k) \
-    case k: consume_library<k, BF16, SMEM_TILE>(a, tile, stages, full, empty, seq, n, t0, m); break;
+    case k: consume_library<k, BF16, SMEM_TILE>(a, tile, stages, full, empty, seq, n, t0, pm); break;
             EDM_CASE(2) EDM_CASE(3) EDM_CASE(4) EDM_CASE(5) EDM_CASE(6) EDM_CASE(7) EDM_CASE(8)
             EDM_CASE(9) EDM_CASE(10) EDM_CASE(11) EDM_CASE(12) EDM_CASE(13) EDM_CASE(14)
             EDM_CASE(15) EDM_CASE(16) EDM_CASE(17) EDM_CASE(18) EDM_CASE(19) EDM_CASE(20)
@@ -429,7 +433,11 @@ __global__ void __launch_bounds__(LkWarps<BF16>::THREADS, 1) lookup_kernel(const
         if (done >= 2) mbar_wait_bounded(&red_empty[p], ((done >> 1) - 1) & 1, a.flags);
         float *rb = red + (p * LK_NC + warp) * NM * 32;
 #pragma unroll
-        for (int j = 0; j < NM; ++j) rb[j * 32 + lane] = m[j];
+        for (int c = 0; c < PairMoments<BF16>::T; ++c) {
+            rb[(3 * c + 0) * 32 + lane] = pm.s[c].x + pm.s[c].y;
+            rb[(3 * c + 1) * 32 + lane] = pm.ss[c].x + pm.ss[c].y;
+            rb[(3 * c + 2) * 32 + lane] = pm.sy[c].x + pm.sy[c].y;
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&red_full[p]);
         ++done;
@@ -446,7 +454,7 @@ edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, cons
     const int nm = bf16 ? 6 : 3;
     const int LK_NC = bf16 ? LkWarps<true>::NC : LkWarps<false>::NC;
     const int threads = bf16 ? LkWarps<true>::THREADS : LkWarps<false>::THREADS;
-    const size_t tile_bytes = static_cast<size_t>(L) * LK_TILE_ROW;
+    const size_t tile_bytes = static_cast<size_t>(L + 1) * LK_TILE_ROW;
     const size_t fixed = static_cast<size_t>(2) * LK_NC * nm * 32 * sizeof(float) +
                          (2 * LK_MAX_STAGES + 5) * sizeof(uint64_t);
     const size_t limit = static_cast<size_t>(ctx->max_smem_optin);
