@@ -179,6 +179,16 @@ edm_status edm_ccm_all(edm_ctx *ctx, const float *X_lib, int N_lib,
                        const int32_t *E_lib, int tau, int Tp,
                        edm_precision prec, float *rho);
 
+/* Convergence with library length (the "convergent" of CCM, section 2.1):
+ * all-to-all CCM restricted to the window X[i][offset .. offset+L_win) of
+ * every series, which serves both as library and as target.  X [N][ld]
+ * float32 (row stride ld >= offset + L_win); E_lib [N] int32 (device);
+ * rho [N][N] float32 as in edm_ccm_all.  Calling it for growing L_win shows
+ * whether the cross-map skill converges. */
+edm_status edm_ccm_window(edm_ctx *ctx, const float *X, int N, int ld, int offset,
+                          int L_win, const int32_t *E_lib, int tau, int Tp,
+                          edm_precision prec, float *rho);
+
 /* One all-to-all CCM problem inside a batch: the series X [N][L] are both
  * the libraries and the targets; only the library rows lib_begin..lib_end-1
  * are computed (so a problem can be split or resumed by row block).

@@ -99,9 +99,11 @@ struct DeviceGuard {
 
 static bool series_len_ok(int L) { return L >= 2 && L <= EDM_L_MAX; }
 
-static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, int N_lib, const float *Y_tgt,
-                          int N_tgt, int L, const int32_t *E_lib, int tau, int Tp,
-                          edm_precision prec, float *rho) {
+// All-to-all CCM of N_lib libraries against N_tgt targets of length L whose
+// rows are ld_lib / ld_tgt floats apart.
+static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, int N_lib,
+                          const float *Y_tgt, long long ld_tgt, int N_tgt, int L,
+                          const int32_t *E_lib, int tau, int Tp, edm_precision prec, float *rho) {
     const size_t yt_bytes = target_store_bytes(N_tgt, L, prec);
     const size_t mean_bytes = align_up(sizeof(double) * N_tgt, 256);
     const size_t sums_bytes = align_up(sizeof(double) * N_tgt * EDM_E_MAX, 256);
@@ -117,11 +119,11 @@ static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, int N_lib, const flo
     double *ysum = reinterpret_cast<double *>(base + yt_bytes + mean_bytes);
     double *yysum = reinterpret_cast<double *>(base + yt_bytes + mean_bytes + sums_bytes);
     uint8_t *tables = base + yt_bytes + mean_bytes + 2 * sums_bytes;
-    st = launch_target_store(ctx, Y_tgt, N_tgt, L, tau, Tp, prec, Yt, mean, ysum, yysum);
+    st = launch_target_store(ctx, Y_tgt, ld_tgt, N_tgt, L, tau, Tp, prec, Yt, mean, ysum, yysum);
     if (st != EDM_OK) return st;
     for (int c0 = 0; c0 < N_lib; c0 += chunk) {
         const int nlib = std::min(chunk, N_lib - c0);
-        st = launch_ccm_tables(ctx, X_lib, c0, nlib, L, E_lib, tau, Tp, tables, slot);
+        st = launch_ccm_tables(ctx, X_lib, ld_lib, c0, nlib, L, E_lib, tau, Tp, tables, slot);
         if (st != EDM_OK) return st;
         st = launch_lookup(ctx, Yt, N_tgt, L, tables, slot, E_lib, c0, nlib, tau, Tp, prec, ysum,
                            yysum, rho + static_cast<size_t>(c0) * N_tgt, N_tgt);
@@ -301,7 +303,19 @@ edm_status edm_ccm_all(edm_ctx *ctx, const float *X_lib, int N_lib, const float 
         tau < 1 || Tp < 0 || L - Tp < 3 || (prec != EDM_FP32 && prec != EDM_BF16_TARGETS))
         return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_all: bad arguments");
     DeviceGuard g(ctx->device);
-    return ccm_one(ctx, X_lib, N_lib, Y_tgt, N_tgt, L, E_lib, tau, Tp, prec, rho);
+    return ccm_one(ctx, X_lib, L, N_lib, Y_tgt, L, N_tgt, L, E_lib, tau, Tp, prec, rho);
+}
+
+edm_status edm_ccm_window(edm_ctx *ctx, const float *X, int N, int ld, int offset, int L_win,
+                          const int32_t *E_lib, int tau, int Tp, edm_precision prec, float *rho) {
+    if (!ctx) return EDM_ERR_INVALID_ARG;
+    if (!X || !E_lib || !rho || N < 1 || offset < 0 || !series_len_ok(L_win) ||
+        static_cast<long long>(offset) + L_win > ld || tau < 1 || Tp < 0 || L_win - Tp < 3 ||
+        (prec != EDM_FP32 && prec != EDM_BF16_TARGETS))
+        return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_window: bad arguments");
+    DeviceGuard g(ctx->device);
+    const float *base = X + offset;
+    return ccm_one(ctx, base, ld, N, base, ld, N, L_win, E_lib, tau, Tp, prec, rho);
 }
 
 edm_status edm_ccm_batched(edm_ctx *ctx, const edm_instance *inst, int n_inst,
@@ -321,9 +335,9 @@ edm_status edm_ccm_batched(edm_ctx *ctx, const edm_instance *inst, int n_inst,
     for (int i = 0; i < n_inst; ++i) {
         const edm_instance &p = inst[i];
         if (p.lib_end == p.lib_begin) continue;
-        edm_status st = ccm_one(ctx, p.X + static_cast<size_t>(p.lib_begin) * p.L,
-                                p.lib_end - p.lib_begin, p.X, p.N, p.L, p.E_lib + p.lib_begin,
-                                p.tau, p.Tp, prec, p.rho);
+        edm_status st = ccm_one(ctx, p.X + static_cast<size_t>(p.lib_begin) * p.L, p.L,
+                                p.lib_end - p.lib_begin, p.X, p.L, p.N, p.L,
+                                p.E_lib + p.lib_begin, p.tau, p.Tp, prec, p.rho);
         if (st != EDM_OK) return st;
     }
     return EDM_OK;

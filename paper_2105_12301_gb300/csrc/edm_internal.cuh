@@ -71,7 +71,8 @@ __host__ __device__ constexpr int table_pair_bytes(int k) {
 edm_status launch_embed(edm_ctx *ctx, const float *x, int L, int E, int tau, float *out);
 edm_status launch_knn(edm_ctx *ctx, const float *X, int N, int L, int E, int tau, int Tp,
                       int k, int32_t *idx, float *dist);
-edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, int lib0, int nlib, int L,
+// X: library series with row stride ld (>= L) floats.
+edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, long long ld, int lib0, int nlib, int L,
                              const int32_t *E_lib, int tau, int Tp, uint8_t *tables,
                              size_t slot_bytes);
 edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max, int tau,
@@ -79,9 +80,10 @@ edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max,
 // Transposed, centred target tiles plus, per E = 1..EDM_E_MAX, the FP64 sums
 // of the stored values and of their squares over the observation window of
 // E (times (E-1)tau+Tp .. L-1): ysum / yysum [EDM_E_MAX][N_tgt].
-edm_status launch_target_store(edm_ctx *ctx, const float *Y, int N_tgt, int L, int tau, int Tp,
-                               edm_precision prec, uint8_t *Yt, double *mean_ws, double *ysum,
-                               double *yysum);
+// Y: target series with row stride ld (>= L) floats.
+edm_status launch_target_store(edm_ctx *ctx, const float *Y, long long ld, int N_tgt, int L,
+                               int tau, int Tp, edm_precision prec, uint8_t *Yt, double *mean_ws,
+                               double *ysum, double *yysum);
 edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L,
                          const uint8_t *tables, size_t slot_bytes, const int32_t *E_lib,
                          int lib0, int nlib, int tau, int Tp, edm_precision prec,

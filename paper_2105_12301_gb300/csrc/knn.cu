@@ -173,9 +173,9 @@ __host__ __device__ inline bool ccm_E_valid(int E, int L, int tau, int Tp) {
 
 template <bool SMEM>
 __global__ void __launch_bounds__(KNN_WARPS * 32)
-    ccm_table_kernel(const float *__restrict__ X, int lib0, int L, const int32_t *__restrict__ E_lib,
-                     int tau, int Tp, int RB, uint8_t *__restrict__ tables, size_t slot_bytes,
-                     int *flags) {
+    ccm_table_kernel(const float *__restrict__ X, long long ld, int lib0, int L,
+                     const int32_t *__restrict__ E_lib, int tau, int Tp, int RB,
+                     uint8_t *__restrict__ tables, size_t slot_bytes, int *flags) {
     extern __shared__ __align__(16) uint8_t smem[];
     WarpScratch *wsa = reinterpret_cast<WarpScratch *>(smem);
     float *xs_s = reinterpret_cast<float *>(smem + KNN_WARPS * sizeof(WarpScratch));
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
     const int n = L - (E - 1) * tau - Tp;
     const int r0 = blockIdx.y * RB, r1 = min(n, r0 + RB);
     if (r0 >= r1) return;
-    const float *xs = stage_series<SMEM>(X + static_cast<size_t>(lib) * L, L, xs_s);
+    const float *xs = stage_series<SMEM>(X + static_cast<size_t>(lib) * ld, L, xs_s);
     WarpScratch *ws = wsa + (threadIdx.x >> 5);
     uint8_t *slot = tables + static_cast<size_t>(blockIdx.x) * slot_bytes;
     switch (E) {
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
 // candidate slot 0 can reach before the start of the series.
 template <int CH, bool HEAD1>
 __global__ void __launch_bounds__(KNN_WARPS * 32)
-    ccm_table_regs_kernel(const float *__restrict__ X, int lib0, int L,
+    ccm_table_regs_kernel(const float *__restrict__ X, long long ld, int lib0, int L,
                           const int32_t *__restrict__ E_lib, int tau, int Tp, int RB,
                           uint8_t *__restrict__ tables, size_t slot_bytes, int *flags) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
     const int lo = (E - 1) * tau, hi = L - 1 - Tp, n = hi - lo + 1;
     const int r0 = blockIdx.y * RB, r1 = min(n, r0 + RB);
     if (r0 >= r1) return;
-    const float *xg = X + static_cast<size_t>(lib) * L;
+    const float *xg = X + static_cast<size_t>(lib) * ld;
     for (int i = threadIdx.x; i < 32 * CH; i += blockDim.x) xs[i] = i < L ? xg[i] : 0.f;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = lane_id();
@@ -270,7 +270,7 @@ size_t ccm_slot_bytes(int L, int tau, int Tp) {
     return align_up(best, 256);
 }
 
-edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, int lib0, int nlib, int L,
+edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, long long ld, int lib0, int nlib, int L,
                              const int32_t *E_lib, int tau, int Tp, uint8_t *tables,
                              size_t slot_bytes) {
     const int n_max = L - Tp;  // rows at E = 1, the most of any E
@@ -283,8 +283,8 @@ edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, int lib0, int nlib, i
         for (int c : CHs)
             if (c >= ch) { CH = c; break; }
         const bool head1 = (EDM_E_MAX - 1) * tau < 32;
-        void (*kern)(const float *, int, int, const int32_t *, int, int, int, uint8_t *, size_t,
-                     int *) = nullptr;
+        void (*kern)(const float *, long long, int, int, const int32_t *, int, int, int, uint8_t *,
+                     size_t, int *) = nullptr;
         switch (CH) {
         case 8: kern = head1 ? ccm_table_regs_kernel<8, true> : ccm_table_regs_kernel<8, false>; break;
         case 16: kern = head1 ? ccm_table_regs_kernel<16, true> : ccm_table_regs_kernel<16, false>; break;
@@ -296,7 +296,7 @@ edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, int lib0, int nlib, i
         const size_t smem = KNN_WARPS * sizeof(WarpScratch) + sizeof(float) * 32 * CH;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         before_launch(ctx);
-        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, lib0, L, E_lib, tau, Tp, RB, tables,
+        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, lib0, L, E_lib, tau, Tp, RB, tables,
                                                           slot_bytes, ctx->d_flags);
         return after_launch(ctx, "ccm_table_kernel");
     }
@@ -306,13 +306,13 @@ edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, int lib0, int nlib, i
         auto kern = ccm_table_kernel<true>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         before_launch(ctx);
-        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, lib0, L, E_lib, tau, Tp, RB, tables,
+        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, lib0, L, E_lib, tau, Tp, RB, tables,
                                                           slot_bytes, ctx->d_flags);
     } else {
         auto kern = ccm_table_kernel<false>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         before_launch(ctx);
-        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, lib0, L, E_lib, tau, Tp, RB, tables,
+        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, lib0, L, E_lib, tau, Tp, RB, tables,
                                                           slot_bytes, ctx->d_flags);
     }
     return after_launch(ctx, "ccm_table_kernel");

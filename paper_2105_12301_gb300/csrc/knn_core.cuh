@@ -315,11 +315,12 @@ __device__ __forceinline__ float warp_sorted_at_f(float v, int r) {
     return __shfl_sync(FULL, v, r);
 }
 
-// Compact the keys (s[j], lane+32j) with s[j] <= bound (and finite, i.e. a
+// Compact the keys (s[j], u0+lane+32j) with s[j] <= bound (and finite, i.e. a
 // candidate of P_E) into ws->key; returns
 // how many there are (only the first KNN_CAP are stored).
 template <int CH>
-__device__ __forceinline__ int compact_le(const float (&s)[CH], float bound, WarpScratch *ws) {
+__device__ __forceinline__ int compact_le(const float (&s)[CH], float bound, WarpScratch *ws,
+                                          int u0 = 0) {
     const int lane = lane_id();
     const unsigned lt = (1u << lane) - 1u;
     int base = 0;
@@ -330,7 +331,7 @@ __device__ __forceinline__ int compact_le(const float (&s)[CH], float bound, War
         if (b) {
             if (p) {
                 const int pos = base + __popc(b & lt);
-                if (pos < KNN_CAP) ws->key[pos] = mk_key(s[j], lane + 32 * j);
+                if (pos < KNN_CAP) ws->key[pos] = mk_key(s[j], u0 + lane + 32 * j);
             }
             base += __popc(b);
         }

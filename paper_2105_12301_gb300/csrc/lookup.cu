@@ -36,11 +36,11 @@ constexpr int LK_TILE_ROW = 128;               // bytes per time row of a tile
 
 // ---------------------------------------------------------- target store
 
-__global__ void target_mean_kernel(const float *__restrict__ Y, int N, int L,
+__global__ void target_mean_kernel(const float *__restrict__ Y, long long ld, int N, int L,
                                    double *__restrict__ mean) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = lane_id();
     if (warp >= N) return;
-    const float *y = Y + static_cast<size_t>(warp) * L;
+    const float *y = Y + static_cast<size_t>(warp) * ld;
     double s = 0.0;
     for (int i = lane; i < L; i += 32) s += static_cast<double>(y[i]);
     s = warp_sum_d(s);
@@ -53,7 +53,7 @@ __global__ void target_mean_kernel(const float *__restrict__ Y, int N, int L,
 // Every tile has L+1 time rows; row L is all zeros (the dummy neighbour row
 // of odd-length tables).
 template <bool BF16>
-__global__ void target_store_kernel(const float *__restrict__ Y, int N, int L,
+__global__ void target_store_kernel(const float *__restrict__ Y, long long ld, int N, int L,
                                     const double *__restrict__ mean, uint8_t *__restrict__ Yt) {
     constexpr int TT = BF16 ? 64 : 32;  // targets per tile
     __shared__ float s[TT][33];
@@ -63,7 +63,7 @@ __global__ void target_store_kernel(const float *__restrict__ Y, int N, int L,
         const int tgt = tile * TT + j, u = u0 + tx;
         float v = 0.f;
         if (tgt < N && u < L)
-            v = static_cast<float>(static_cast<double>(Y[static_cast<size_t>(tgt) * L + u]) -
+            v = static_cast<float>(static_cast<double>(Y[static_cast<size_t>(tgt) * ld + u]) -
                                    mean[tgt]);
         s[j][tx] = v;
     }
@@ -141,12 +141,12 @@ size_t target_store_bytes(int N_tgt, int L, edm_precision prec) {
     return align_up(tiles * (L + 1) * LK_TILE_ROW, 256);
 }
 
-edm_status launch_target_store(edm_ctx *ctx, const float *Y, int N_tgt, int L, int tau, int Tp,
-                               edm_precision prec, uint8_t *Yt, double *mean_ws, double *ysum,
-                               double *yysum) {
+edm_status launch_target_store(edm_ctx *ctx, const float *Y, long long ld, int N_tgt, int L,
+                               int tau, int Tp, edm_precision prec, uint8_t *Yt, double *mean_ws,
+                               double *ysum, double *yysum) {
     const int warps_blocks = (N_tgt * 32 + 255) / 256;
     before_launch(ctx);
-    target_mean_kernel<<<warps_blocks, 256, 0, ctx->stream>>>(Y, N_tgt, L, mean_ws);
+    target_mean_kernel<<<warps_blocks, 256, 0, ctx->stream>>>(Y, ld, N_tgt, L, mean_ws);
     edm_status st = after_launch(ctx, "target_mean_kernel");
     if (st != EDM_OK) return st;
     const int tt = targets_per_tile(prec);
@@ -154,9 +154,9 @@ edm_status launch_target_store(edm_ctx *ctx, const float *Y, int N_tgt, int L, i
     const bool bf16 = prec == EDM_BF16_TARGETS;
     before_launch(ctx);
     if (bf16)
-        target_store_kernel<true><<<grid, block, 0, ctx->stream>>>(Y, N_tgt, L, mean_ws, Yt);
+        target_store_kernel<true><<<grid, block, 0, ctx->stream>>>(Y, ld, N_tgt, L, mean_ws, Yt);
     else
-        target_store_kernel<false><<<grid, block, 0, ctx->stream>>>(Y, N_tgt, L, mean_ws, Yt);
+        target_store_kernel<false><<<grid, block, 0, ctx->stream>>>(Y, ld, N_tgt, L, mean_ws, Yt);
     st = after_launch(ctx, "target_store_kernel");
     if (st != EDM_OK) return st;
     before_launch(ctx);

@@ -202,6 +202,199 @@ __global__ void __launch_bounds__(SX_WARPS * 32)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Incremental sweep for long series (more than 2,048 points).
+//
+// The candidates of a query time are visited in chunks of 1,024 (32 slots per
+// lane in registers); within a chunk every E extends the distances by one lag
+// exactly as in sweep_row.  Each E keeps, in the warp's shared memory, the
+// running list of its R = E+2 smallest FP32 keys over the chunks seen so far,
+// sorted.  A chunk only needs the values at or below the list's last key (or,
+// while the list is not yet full, below the R-th smallest lane minimum of the
+// chunk); those are compacted, merged with the list and ranked.  After the
+// last chunk every E has its exact FP32 top-R, and the band check of
+// knn_row's KNN_SET mode decides whether the FP64 ranking must be consulted.
+
+constexpr int LS_CH = 32;          // candidate slots per lane per chunk
+constexpr int LS_LIST = 256;       // sum over E = 1..20 of (E+2) = 250 keys
+
+__device__ __forceinline__ int ls_list_off(int E) { return (E - 1) * (E + 4) / 2; }
+
+// FP32 squared distance with E a run-time value: the same operations in the
+// same order as dist32<E>.
+__device__ __forceinline__ float dist32_rt(const float *xs, int t, int u, int E, int tau) {
+    float s = 0.f;
+    for (int l = 0; l < E; ++l) {
+        const float d = __fsub_rn(xs[t - l * tau], xs[u - l * tau]);
+        s = __fmaf_rn(d, d, s);
+    }
+    return s;
+}
+
+struct LongScratch {
+    WarpScratch ws;
+    uint64_t list[LS_LIST];   // per E: its R smallest keys so far, ascending
+};
+
+__device__ void sweep_long_row(const float *xs, int L, int t, int hi, int E_max, int tau, int Tp,
+                               float mu, LongScratch *sc, float (&m)[5]) {
+    const int lane = lane_id();
+    WarpScratch *ws = &sc->ws;
+    // last E for which t is a point of P_E with enough points
+    int E_row = 0;
+    for (int E = 1; E <= E_max; ++E) {
+        const int lo = (E - 1) * tau;
+        if (t < lo || hi - lo + 1 < E + 2) break;
+        E_row = E;
+    }
+    int cnt = 0;    // lane e: keys held in the list of E = e+1
+    int degen = 0;  // lane e: E = e+1 has too many ties for the list
+    for (int c0 = 0; c0 <= hi; c0 += 32 * LS_CH) {
+        float s[LS_CH];
+#pragma unroll
+        for (int j = 0; j < LS_CH; ++j) {
+            const int u = c0 + lane + 32 * j;
+            s[j] = (u <= hi && u != t) ? 0.f : EDM_INF;
+        }
+        for (int E = 1; E <= E_row; ++E) {
+            const int lo = (E - 1) * tau;
+            const float qv = xs[t - lo];
+#pragma unroll
+            for (int j = 0; j < LS_CH; ++j) {
+                const int u = c0 + lane + 32 * j;
+                const float d = __fsub_rn(qv, xs[min(max(u - lo, 0), L - 1)]);
+                const float v = __fmaf_rn(d, d, s[j]);
+                s[j] = (u < lo) ? EDM_INF : v;
+            }
+            const int R = min(E + 2, hi - lo);
+            uint64_t *list = sc->list + ls_list_off(E);
+            const int have = __shfl_sync(FULL, cnt, E - 1);
+            float bound = have == R ? key_s(list[R - 1]) : EDM_INF;
+            if (have < R) {
+                float lmin = EDM_INF;
+#pragma unroll
+                for (int j = 0; j < LS_CH; ++j) lmin = fminf(lmin, s[j]);
+                bound = fminf(bound, warp_sorted_at_f(lmin, min(R, 32) - 1));
+            }
+            if (__shfl_sync(FULL, degen, E - 1)) continue;
+            const int c = compact_le<LS_CH>(s, bound, ws, c0);
+            if (c > KNN_CAP - 32) {
+                // more values tie at the bound than the buffer holds (long
+                // runs of repeated values): this E is resolved in FP64 below
+                if (lane == E - 1) degen = 1;
+                continue;
+            }
+            if (c == 0) continue;
+            // merge the collected keys with the list and keep the R smallest
+            for (int e = lane; e < have; e += 32) ws->key[c + e] = list[e];
+            __syncwarp();
+            const int tot = c + have;
+            rank_keys(ws, tot, min(R, tot));
+            const int keep = min(R, tot);
+            for (int e = lane; e < keep; e += 32) list[e] = ws->sel[e];
+            __syncwarp();
+            if (lane == E - 1) cnt = keep;
+        }
+    }
+    // every E now holds its exact FP32 top-R: band check, weights, moments
+    for (int E = 1; E <= E_row; ++E) {
+        const int lo = (E - 1) * tau, K = E + 1;
+        const int R = min(E + 2, hi - lo);
+        const uint64_t *list = sc->list + ls_list_off(E);
+        int u_out = 0;
+        float d_out = 0.f;
+        const bool deg = __shfl_sync(FULL, degen, E - 1) != 0;
+        const float edge = deg ? 0.f : band_edge(key_s(list[K - 1]), E);
+        if (deg) {
+            brute_fp64(xs, t, lo, hi, E, tau, ws, K);
+            if (lane < K) {
+                u_out = ws->sel_u[lane];
+                d_out = __double2float_rn(__dsqrt_rn(ws->sel_s64[lane]));
+            }
+        } else if (R <= K || key_s(list[K]) > edge) {
+            if (lane < K) {
+                u_out = key_u(list[lane]);
+                d_out = sqrtf(key_s(list[lane]));
+            }
+        } else {
+            if (lane == 0) ws->count = 0;
+            __syncwarp();
+            for (int u = lo + lane; u <= hi; u += 32) {
+                if (u == t) continue;
+                const float v = dist32_rt(xs, t, u, E, tau);
+                if (v <= edge) {
+                    const int pos = atomicAdd(&ws->count, 1);
+                    if (pos < KNN_CAP) ws->key[pos] = mk_key(v, u);
+                }
+            }
+            __syncwarp();
+            const int c = ws->count;
+            __syncwarp();
+            if (c <= KNN_CAP)
+                rank_band_fp64(xs, t, E, tau, ws, c, K);
+            else
+                brute_fp64(xs, t, lo, hi, E, tau, ws, K);
+            if (lane < K) {
+                u_out = ws->sel_u[lane];
+                d_out = __double2float_rn(__dsqrt_rn(ws->sel_s64[lane]));
+            }
+        }
+        __syncwarp();
+        const float w = simplex_weight(d_out, K);
+        const float part = lane < K ? w * __fsub_rn(xs[u_out + Tp], mu) : 0.f;
+        const float a = warp_sum(part);
+        const float b = __fsub_rn(xs[t + Tp], mu);
+        if (lane == E - 1) {
+            m[0] += a;
+            m[1] += b;
+            m[2] = __fmaf_rn(a, a, m[2]);
+            m[3] = __fmaf_rn(b, b, m[3]);
+            m[4] = __fmaf_rn(a, b, m[4]);
+        }
+    }
+}
+
+template <bool SMEM>
+__global__ void __launch_bounds__(SX_WARPS * 32)
+    sweep_long_kernel(const float *__restrict__ X, int L, int E_max, int tau, int Tp, int TB,
+                      int nrb, double *__restrict__ partial) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    LongScratch *sca = reinterpret_cast<LongScratch *>(smem);
+    float *red = reinterpret_cast<float *>(smem + SX_WARPS * sizeof(LongScratch));
+    double *mu_s = reinterpret_cast<double *>(red + SX_WARPS * 32 * 5);
+    float *xs_s = reinterpret_cast<float *>(mu_s + SX_WARPS);
+    const int series = blockIdx.x, rb = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    const float *xg = X + static_cast<size_t>(series) * L;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) acc += static_cast<double>(xg[i]);
+    acc = warp_sum_d(acc);
+    if (lane == 0) mu_s[warp] = acc;
+    const float *xs = xg;
+    if (SMEM) {
+        for (int i = threadIdx.x; i < L; i += blockDim.x) xs_s[i] = xg[i];
+        xs = xs_s;
+    }
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < SX_WARPS; ++w) tot += mu_s[w];
+    const float mu = static_cast<float>(tot / L);
+    float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    const int hi = L - 1 - Tp;
+    const int t1 = min(hi + 1, (rb + 1) * TB);
+    for (int t = rb * TB + warp; t < t1; t += SX_WARPS)
+        sweep_long_row(xs, L, t, hi, E_max, tau, Tp, mu, sca + warp, m);
+#pragma unroll
+    for (int j = 0; j < 5; ++j) red[(warp * 32 + lane) * 5 + j] = m[j];
+    __syncthreads();
+    for (int i = threadIdx.x; i < E_max * 5; i += blockDim.x) {
+        const int e = i / 5, j = i % 5;
+        double sum = 0.0;
+        for (int w = 0; w < SX_WARPS; ++w) sum += static_cast<double>(red[(w * 32 + e) * 5 + j]);
+        partial[((static_cast<size_t>(series) * nrb + rb) * E_max + e) * 5 + j] = sum;
+    }
+}
+
 // One thread per series: sum the partials, rho per E, argmax.
 __global__ void simplex_finish_kernel(const double *__restrict__ partial, int N, int L, int E_max,
                                       int tau, int Tp, int nrb, int32_t *__restrict__ E_opt,
@@ -280,19 +473,15 @@ edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max,
         st = after_launch(ctx, "sweep_kernel");
         if (st != EDM_OK) return st;
     } else {
+        // long series: chunked incremental sweep
+        const size_t lfixed = SX_WARPS * sizeof(LongScratch) + SX_WARPS * 32 * 5 * sizeof(float) +
+                              SX_WARPS * sizeof(double);
         const bool smem_series = sizeof(float) * static_cast<size_t>(L) <= SX_SERIES_SMEM_MAX;
-        const size_t smem = fixed + (smem_series ? align_up(sizeof(float) * L, 16) : 0);
-        if (smem_series) {
-            auto kern = simplex_kernel<true>;
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            before_launch(ctx);
-            kern<<<grid, SX_WARPS * 32, smem, ctx->stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial);
-        } else {
-            auto kern = simplex_kernel<false>;
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            before_launch(ctx);
-            kern<<<grid, SX_WARPS * 32, smem, ctx->stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial);
-        }
+        const size_t smem = lfixed + (smem_series ? align_up(sizeof(float) * L, 16) : 0);
+        auto kern = smem_series ? sweep_long_kernel<true> : sweep_long_kernel<false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        before_launch(ctx);
+        kern<<<grid, SX_WARPS * 32, smem, ctx->stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial);
         st = after_launch(ctx, "simplex_kernel");
         if (st != EDM_OK) return st;
     }

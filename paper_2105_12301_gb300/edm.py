@@ -71,6 +71,7 @@ def load():
     lib.edm_simplex_optimal_E.argtypes = [vp, vp, ci, ci, ci, ci, ci, vp, vp]
     lib.edm_ccm_all.argtypes = [vp, vp, ci, vp, ci, ci, vp, ci, ci, ci, vp]
     lib.edm_ccm_batched.argtypes = [vp, ctypes.POINTER(edm_instance), ci, ci]
+    lib.edm_ccm_window.argtypes = [vp, vp, ci, ci, ci, ci, vp, ci, ci, ci, vp]
     lib.edm_simplex_optimal_E_noalloc.argtypes = [vp, ci, ci, ci, ci, ci, vp, vp, vp]
     lib.edm_profile_enable.argtypes = [vp, ci]
     lib.edm_profile_read.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
@@ -80,7 +81,7 @@ def load():
     for f in ("edm_create", "edm_destroy", "edm_set_stream", "edm_ctx_sync", "edm_embed",
               "edm_knn", "edm_simplex_optimal_E", "edm_ccm_all", "edm_ccm_batched",
               "edm_profile_enable", "edm_profile_read", "edm_probe_smem_bandwidth",
-              "edm_simplex_optimal_E_noalloc"):
+              "edm_simplex_optimal_E_noalloc", "edm_ccm_window"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -247,6 +248,19 @@ def edm_ccm_all(X_lib, Y_tgt, E_lib, tau=1, Tp=0, precision="fp32", out=None):
     ctx = _ctx(X_lib.device)
     _check(ctx, load().edm_ccm_all(ctx, _ptr(X_lib), N_lib, _ptr(Y_tgt), N_tgt, L, _ptr(E_lib),
                                    tau, Tp, _prec(precision), _ptr(rho)), "edm_ccm_all")
+    return rho
+
+
+def edm_ccm_window(X, offset, L_win, E_lib, tau=1, Tp=0, precision="fp32", out=None):
+    """rho [N][N] of all-to-all CCM on the windows X[:, offset:offset+L_win]."""
+    _series(X, "X", 2)
+    N, ld = X.shape
+    if E_lib.dtype != torch.int32 or not E_lib.is_cuda or E_lib.shape != (N,):
+        raise TypeError("E_lib must be a CUDA int32 tensor of shape [N]")
+    rho = out if out is not None else torch.empty((N, N), dtype=torch.float32, device=X.device)
+    ctx = _ctx(X.device)
+    _check(ctx, load().edm_ccm_window(ctx, _ptr(X), N, ld, offset, L_win, _ptr(E_lib.contiguous()),
+                                      tau, Tp, _prec(precision), _ptr(rho)), "edm_ccm_window")
     return rho
 
 

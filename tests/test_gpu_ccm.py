@@ -168,3 +168,30 @@ def test_register_path_boundaries(L, tau):
     E_lib = np.array([2, 5, 1, 3, 4, 6], np.int32)
     E_lib[:3] = E
     check_ccm(X, X, E_lib, tau, 0, "fp32", TOL_FP32, lib_rows=[0, 4])
+
+
+@pytest.mark.parametrize("L,tau,Tp_sel", [(3100, 1, 1), (2600, 2, 1), (4000, 1, 2)])
+def test_optimal_E_long_series(L, tau, Tp_sel):
+    # more than 2,048 points: the chunked incremental sweep
+    X = inputs.coupled_logistic(3, L, 70 + L)
+    check_optimal_E(X, 6, tau, Tp_sel)
+
+
+def test_window_convergence_matches_oracle():
+    # library-length windows [0, Lw) of longer series, as in the convergence sweep
+    X = inputs.coupled_logistic(24, 1200, 91)
+    Xg = gpu(X)
+    E_full, _ = edm.edm_simplex_optimal_E(Xg, 8, 1, 1)
+    E_np = E_full.cpu().numpy()
+    for Lw in (100, 300, 1200):
+        rho = edm.edm_ccm_window(Xg, 0, Lw, E_full, 1, 0, "fp32")
+        edm.edm_ctx_sync()
+        ref = oracle.ccm_matrix(X[:, :Lw], X[:, :Lw], E_np, 1, 0, lib_rows=[0, 7, 23])
+        got = rho.cpu().numpy()[[0, 7, 23]]
+        np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+        ok = ~np.isnan(ref)
+        assert np.max(np.abs(got[ok] - ref[ok])) <= TOL_FP32
+    # an offset window
+    rho = edm.edm_ccm_window(Xg, 200, 500, E_full, 1, 0, "bf16").cpu().numpy()
+    ref = oracle.ccm_matrix(X[:, 200:700], X[:, 200:700], E_np, 1, 0, lib_rows=[3])
+    assert np.max(np.abs(rho[3] - ref[0])) <= TOL_BF16
