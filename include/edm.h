@@ -207,9 +207,35 @@ typedef struct edm_instance {
 
 /* Run n_inst independent CCM problems of uneven N and L.  `inst` is a HOST
  * array of n_inst descriptors (read before the call returns); the pointers
- * inside are device pointers.  Same per-instance rules as edm_ccm_all. */
+ * inside are device pointers.  Same per-instance rules as edm_ccm_all.
+ * Execution (no counterpart in the paper): the instances are spread over
+ * several internal streams, largest first, each stream with its own
+ * workspace; by default the whole batch is captured once into a CUDA graph
+ * and the graph is replayed when the same batch (same descriptors) comes
+ * again.  Before the first capture the autotuner times the lookup's number
+ * of libraries per CTA for every new size bucket of the batch.  The work is
+ * ordered after what was queued on the context's stream before the call and
+ * before what is queued after it. */
 edm_status edm_ccm_batched(edm_ctx *ctx, const edm_instance *inst, int n_inst,
                            edm_precision prec);
+
+/* Optimal E (as edm_simplex_optimal_E) of every series of every instance,
+ * batched like edm_ccm_batched.  Only X, N, L and tau of each descriptor are
+ * used; E_out is a HOST array of n_inst DEVICE pointers, E_out[i] [N_i]
+ * int32. */
+edm_status edm_simplex_optimal_E_batched(edm_ctx *ctx, const edm_instance *inst,
+                                         int n_inst, int E_max, int Tp_sel,
+                                         int32_t *const *E_out);
+
+/* Execution options (no counterpart in the paper):
+ *   "batch_streams"        1..32  concurrent streams of batched calls (8)
+ *   "batch_graph"          0/1    capture batched calls into a CUDA graph (1)
+ *   "autotune"             0/1    tune the lookup's libraries per CTA (1)
+ *   "lookup_libs_per_cta"  0..4096 fixed libraries per CTA, 0 = tuned (0)
+ *   "table_budget_mb"      >= 16  workspace for neighbour tables (2048)
+ *   "autotune_reset"       1      forget the tuned values
+ * Returns EDM_ERR_INVALID_ARG for an unknown name or value. */
+edm_status edm_set_option(edm_ctx *ctx, const char *name, long long value);
 
 #ifdef __cplusplus
 }

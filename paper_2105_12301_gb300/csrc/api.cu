@@ -101,6 +101,16 @@ static bool series_len_ok(int L) { return L >= 2 && L <= EDM_L_MAX; }
 
 // All-to-all CCM of N_lib libraries against N_tgt targets of length L whose
 // rows are ld_lib / ld_tgt floats apart.
+static size_t ccm_workspace_bytes(edm_ctx *ctx, int N_lib, int N_tgt, int L, int tau, int Tp,
+                                  edm_precision prec) {
+    const size_t yt_bytes = target_store_bytes(N_tgt, L, prec);
+    const size_t mean_bytes = align_up(sizeof(double) * N_tgt, 256);
+    const size_t sums_bytes = align_up(sizeof(double) * N_tgt * EDM_E_MAX, 256);
+    const size_t slot = ccm_slot_bytes(L, tau, Tp);
+    const size_t chunk = slot ? std::max<size_t>(1, std::min<size_t>(N_lib, ctx->table_budget / slot)) : 1;
+    return yt_bytes + mean_bytes + 2 * sums_bytes + chunk * slot;
+}
+
 static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, int N_lib,
                           const float *Y_tgt, long long ld_tgt, int N_tgt, int L,
                           const int32_t *E_lib, int tau, int Tp, edm_precision prec, float *rho) {
@@ -111,7 +121,7 @@ static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, in
     if (slot == 0) return set_error(ctx, EDM_ERR_INVALID_ARG, "series too short");
     const int chunk = static_cast<int>(
         std::max<size_t>(1, std::min<size_t>(N_lib, ctx->table_budget / slot)));
-    edm_status st = ws_reserve(ctx, yt_bytes + mean_bytes + 2 * sums_bytes + chunk * slot);
+    edm_status st = ws_reserve(ctx, ccm_workspace_bytes(ctx, N_lib, N_tgt, L, tau, Tp, prec));
     if (st != EDM_OK) return st;
     uint8_t *base = static_cast<uint8_t *>(ctx->ws);
     uint8_t *Yt = base;
@@ -128,6 +138,197 @@ static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, in
         st = launch_lookup(ctx, Yt, N_tgt, L, tables, slot, E_lib, c0, nlib, tau, Tp, prec, ysum,
                            yysum, rho + static_cast<size_t>(c0) * N_tgt, N_tgt);
         if (st != EDM_OK) return st;
+    }
+    return EDM_OK;
+}
+
+
+// ------------------------------------------------------------ batched calls
+
+static edm_ctx *make_sub(edm_ctx *main) {
+    edm_ctx *sub = new (std::nothrow) edm_ctx();
+    if (!sub) return nullptr;
+    sub->device = main->device;
+    sub->num_sms = main->num_sms;
+    sub->max_smem_optin = main->max_smem_optin;
+    sub->d_flags = main->d_flags;
+    sub->table_budget = main->table_budget;
+    sub->tune = main->tune;
+    sub->is_sub = true;
+    if (cudaStreamCreateWithFlags(&sub->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete sub;
+        return nullptr;
+    }
+    return sub;
+}
+
+static void free_sub(edm_ctx *sub) {
+    cudaStreamSynchronize(sub->stream);
+    if (sub->ws) cudaFree(sub->ws);
+    prof_clear(sub);
+    for (cudaEvent_t e : sub->prof_pool) cudaEventDestroy(e);
+    cudaStreamDestroy(sub->stream);
+    delete sub;
+}
+
+static edm_status ensure_batch_state(edm_ctx *ctx, int S) {
+    if (!ctx->origin && cudaStreamCreateWithFlags(&ctx->origin, cudaStreamNonBlocking) != cudaSuccess)
+        return set_error(ctx, EDM_ERR_CUDA, "batch stream creation failed");
+    if (!ctx->ev_fork && cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+        return set_error(ctx, EDM_ERR_CUDA, "batch event creation failed");
+    if (!ctx->ev_done && cudaEventCreateWithFlags(&ctx->ev_done, cudaEventDisableTiming) != cudaSuccess)
+        return set_error(ctx, EDM_ERR_CUDA, "batch event creation failed");
+    while (static_cast<int>(ctx->subs.size()) < S) {
+        edm_ctx *sub = make_sub(ctx);
+        if (!sub) return set_error(ctx, EDM_ERR_CUDA, "batch stream creation failed");
+        ctx->subs.push_back(sub);
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return set_error(ctx, EDM_ERR_CUDA, "batch event creation failed");
+        ctx->ev_join.push_back(e);
+    }
+    return EDM_OK;
+}
+
+static uint64_t fnv1a(uint64_t h, const void *p, size_t n) {
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    return h;
+}
+
+// Time the kernels named `kernel` launched by fn(sub) on a sub-context (ms).
+template <class Fn>
+static double time_kernel_ms(edm_ctx *sub, const char *kernel, Fn fn, edm_status &st) {
+    cudaStreamSynchronize(sub->stream);
+    prof_clear(sub);
+    sub->prof_on = true;
+    st = fn();
+    sub->prof_on = false;
+    cudaStreamSynchronize(sub->stream);
+    double tot = 0.0;
+    for (auto &r : sub->prof) {
+        if (strcmp(r.kernel, kernel) != 0) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.start, r.stop);
+        tot += ms;
+    }
+    prof_clear(sub);
+    return tot;
+}
+
+// Run fn(sub, i) for every instance i on S concurrent sub-streams, the
+// largest work first to the least-loaded stream; when enabled, the whole
+// fork/join is captured once into a CUDA graph (cached under `key`) and
+// replayed.  Work queued on ctx->stream before the call runs first; work
+// queued after it waits for the batch.
+template <class Fn>
+static edm_status run_batched(edm_ctx *ctx, int n, const std::vector<double> &work,
+                              const std::vector<size_t> &ws_need, uint64_t key, Fn fn) {
+    const int S = std::max(1, std::min({ctx->batch_streams, n, 32}));
+    edm_status st = ensure_batch_state(ctx, S);
+    if (st != EDM_OK) return st;
+    std::vector<int> order(n), assign(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    std::vector<double> load(S, 0.0);
+    std::vector<size_t> need(S, 0);
+    for (int i : order) {
+        const int s = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
+        assign[i] = s;
+        load[s] += work[i];
+        need[s] = std::max(need[s], ws_need[i]);
+    }
+    for (int s = 0; s < S; ++s) {
+        edm_ctx *sub = ctx->subs[s];
+        sub->table_budget = ctx->table_budget;
+        sub->autotune = ctx->autotune;
+        sub->lookup_lb = ctx->lookup_lb;
+        st = ws_reserve(sub, need[s]);
+        if (st != EDM_OK) return set_error(ctx, st, "%s", sub->last_error);
+    }
+    auto enqueue = [&](cudaStream_t from) -> edm_status {
+        if (cudaEventRecord(ctx->ev_fork, from) != cudaSuccess)
+            return set_error(ctx, EDM_ERR_CUDA, "batch fork failed");
+        for (int s = 0; s < S; ++s) cudaStreamWaitEvent(ctx->subs[s]->stream, ctx->ev_fork, 0);
+        for (int i : order) {
+            edm_status e = fn(ctx->subs[assign[i]], i);
+            if (e != EDM_OK) return set_error(ctx, e, "instance %d: %s", i, ctx->subs[assign[i]]->last_error);
+        }
+        for (int s = 0; s < S; ++s) {
+            cudaEventRecord(ctx->ev_join[s], ctx->subs[s]->stream);
+            cudaStreamWaitEvent(from, ctx->ev_join[s], 0);
+        }
+        return EDM_OK;
+    };
+    uint64_t before = 0;
+    for (int s = 0; s < S; ++s) before += ctx->subs[s]->launches;
+    if (!ctx->batch_graph) {
+        st = enqueue(ctx->stream);
+        for (int s = 0; s < S; ++s) ctx->launches += ctx->subs[s]->launches;
+        ctx->launches -= before;
+        return st;
+    }
+    key = fnv1a(key, &S, sizeof(S));
+    if (!ctx->graph_exec || ctx->graph_key != key) {
+        if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+        if (cudaStreamBeginCapture(ctx->origin, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+            return set_error(ctx, EDM_ERR_CUDA, "graph capture could not begin");
+        st = enqueue(ctx->origin);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(ctx->origin, &graph);
+        if (st != EDM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (ce != cudaSuccess || !graph) return cuda_check(ctx, ce, "graph capture");
+        const cudaError_t ie = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return cuda_check(ctx, ie, "graph instantiation");
+        ctx->graph_key = key;
+        uint64_t after = 0;
+        for (int s = 0; s < S; ++s) after += ctx->subs[s]->launches;
+        ctx->graph_kernels = after - before;
+    }
+    // order the replay after the caller's stream, and the caller's stream after it
+    if (cudaEventRecord(ctx->ev_fork, ctx->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(ctx->origin, ctx->ev_fork, 0) != cudaSuccess)
+        return set_error(ctx, EDM_ERR_CUDA, "batch ordering failed");
+    st = cuda_check(ctx, cudaGraphLaunch(ctx->graph_exec, ctx->origin), "graph launch");
+    if (st != EDM_OK) return st;
+    cudaEventRecord(ctx->ev_done, ctx->origin);
+    cudaStreamWaitEvent(ctx->stream, ctx->ev_done, 0);
+    ctx->launches += ctx->graph_kernels;
+    return EDM_OK;
+}
+
+// Autotuner: for every lookup bucket of the batch not tuned yet, time the
+// lookup of its first instance with each candidate number of libraries per
+// CTA and keep the fastest (before capture: timing needs synchronisation).
+template <class Fn>
+static edm_status autotune_lookup(edm_ctx *ctx, int n, const std::vector<uint64_t> &bucket, Fn fn) {
+    if (!ctx->autotune || ctx->lookup_lb > 0) return EDM_OK;
+    edm_ctx *sub = ctx->subs[0];
+    for (int i = 0; i < n; ++i) {
+        if (ctx->tune->count(bucket[i])) continue;
+        int best = 0;
+        double best_ms = 0.0;
+        for (int cand = 1; cand <= 128; cand *= 2) {
+            sub->lookup_lb = cand;
+            edm_status st = EDM_OK;
+            const double ms = time_kernel_ms(sub, "lookup_kernel", [&] { return fn(sub, i); }, st);
+            if (st != EDM_OK) {
+                sub->lookup_lb = 0;
+                return st;
+            }
+            if (best == 0 || ms < best_ms) {
+                best = cand;
+                best_ms = ms;
+            }
+        }
+        sub->lookup_lb = 0;
+        (*ctx->tune)[bucket[i]] = best;
+        ctx->graph_key = 0;  // a captured graph may hold the old choice
     }
     return EDM_OK;
 }
@@ -165,6 +366,7 @@ edm_status edm_create(edm_ctx **out, int device, void *cuda_stream) {
     ctx->device = device;
     ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     ctx->table_budget = static_cast<size_t>(2) << 30;
+    ctx->tune = new (std::nothrow) std::map<uint64_t, int>();
     if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) !=
             cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
@@ -184,10 +386,17 @@ edm_status edm_destroy(edm_ctx *ctx) {
     if (!ctx) return EDM_ERR_INVALID_ARG;
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    for (edm_ctx *sub : ctx->subs) free_sub(sub);
+    for (cudaEvent_t e : ctx->ev_join) cudaEventDestroy(e);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_done) cudaEventDestroy(ctx->ev_done);
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->origin) cudaStreamDestroy(ctx->origin);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->d_flags) cudaFree(ctx->d_flags);
     prof_clear(ctx);
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+    delete ctx->tune;
     delete ctx;
     return EDM_OK;
 }
@@ -318,28 +527,110 @@ edm_status edm_ccm_window(edm_ctx *ctx, const float *X, int N, int ld, int offse
     return ccm_one(ctx, base, ld, N, base, ld, N, L_win, E_lib, tau, Tp, prec, rho);
 }
 
+static bool instance_ok(const edm_instance &p) {
+    return p.X && p.E_lib && p.N >= 1 && series_len_ok(p.L) && p.tau >= 1 && p.Tp >= 0 &&
+           p.L - p.Tp >= 3 && p.lib_begin >= 0 && p.lib_end <= p.N && p.lib_begin <= p.lib_end;
+}
+
 edm_status edm_ccm_batched(edm_ctx *ctx, const edm_instance *inst, int n_inst,
                            edm_precision prec) {
     if (!ctx) return EDM_ERR_INVALID_ARG;
     if (!inst || n_inst < 0 || (prec != EDM_FP32 && prec != EDM_BF16_TARGETS))
         return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_batched: bad arguments");
-    for (int i = 0; i < n_inst; ++i) {
-        const edm_instance &p = inst[i];
-        if (!p.X || !p.E_lib || !p.rho || p.N < 1 || !series_len_ok(p.L) || p.tau < 1 ||
-            p.Tp < 0 || p.L - p.Tp < 3 || p.lib_begin < 0 || p.lib_end > p.N ||
-            p.lib_begin > p.lib_end)
+    for (int i = 0; i < n_inst; ++i)
+        if (!instance_ok(inst[i]) || !inst[i].rho)
             return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_batched: instance %d is invalid",
                              i);
-    }
     DeviceGuard g(ctx->device);
+    std::vector<int> live;
+    for (int i = 0; i < n_inst; ++i)
+        if (inst[i].lib_end > inst[i].lib_begin) live.push_back(i);
+    const int n = static_cast<int>(live.size());
+    if (n == 0) return EDM_OK;
+    std::vector<double> work(n);
+    std::vector<size_t> need(n);
+    std::vector<uint64_t> bucket(n);
+    uint64_t key = 1469598103934665603ull;
+    key = fnv1a(key, "ccm", 3);
+    key = fnv1a(key, &prec, sizeof(prec));
+    for (int j = 0; j < n; ++j) {
+        const edm_instance &p = inst[live[j]];
+        const int nl = p.lib_end - p.lib_begin;
+        work[j] = static_cast<double>(nl) * p.N * p.L;
+        need[j] = ccm_workspace_bytes(ctx, nl, p.N, p.L, p.tau, p.Tp, prec);
+        bucket[j] = lookup_bucket(p.L, p.N, nl, prec);
+        key = fnv1a(key, &p, sizeof(p));
+    }
+    auto fn = [&](edm_ctx *sub, int j) {
+        const edm_instance &p = inst[live[j]];
+        return ccm_one(sub, p.X + static_cast<size_t>(p.lib_begin) * p.L, p.L,
+                       p.lib_end - p.lib_begin, p.X, p.L, p.N, p.L, p.E_lib + p.lib_begin, p.tau,
+                       p.Tp, prec, p.rho);
+    };
+    edm_status st = ensure_batch_state(ctx, std::max(1, std::min({ctx->batch_streams, n, 32})));
+    if (st != EDM_OK) return st;
+    st = ws_reserve(ctx->subs[0], *std::max_element(need.begin(), need.end()));
+    if (st != EDM_OK) return st;
+    st = autotune_lookup(ctx, n, bucket, fn);
+    if (st != EDM_OK) return st;
+    for (auto &kv : *ctx->tune) key = fnv1a(key, &kv, sizeof(kv));
+    key = fnv1a(key, &ctx->lookup_lb, sizeof(ctx->lookup_lb));
+    key = fnv1a(key, &ctx->autotune, sizeof(ctx->autotune));
+    return run_batched(ctx, n, work, need, key, fn);
+}
+
+edm_status edm_simplex_optimal_E_batched(edm_ctx *ctx, const edm_instance *inst, int n_inst,
+                                         int E_max, int Tp_sel, int32_t *const *E_out) {
+    if (!ctx) return EDM_ERR_INVALID_ARG;
+    if (!inst || !E_out || n_inst < 0 || E_max < 1 || E_max > EDM_E_MAX || Tp_sel < 0)
+        return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_simplex_optimal_E_batched: bad arguments");
     for (int i = 0; i < n_inst; ++i) {
         const edm_instance &p = inst[i];
-        if (p.lib_end == p.lib_begin) continue;
-        edm_status st = ccm_one(ctx, p.X + static_cast<size_t>(p.lib_begin) * p.L, p.L,
-                                p.lib_end - p.lib_begin, p.X, p.L, p.N, p.L,
-                                p.E_lib + p.lib_begin, p.tau, p.Tp, prec, p.rho);
-        if (st != EDM_OK) return st;
+        if (!p.X || !E_out[i] || p.N < 1 || !series_len_ok(p.L) || p.tau < 1 || p.L - Tp_sel < 3)
+            return set_error(ctx, EDM_ERR_INVALID_ARG,
+                             "edm_simplex_optimal_E_batched: instance %d is invalid", i);
     }
+    if (n_inst == 0) return EDM_OK;
+    DeviceGuard g(ctx->device);
+    std::vector<double> work(n_inst);
+    std::vector<size_t> need(n_inst);
+    uint64_t key = 1469598103934665603ull;
+    key = fnv1a(key, "simplex", 7);
+    key = fnv1a(key, &E_max, sizeof(E_max));
+    key = fnv1a(key, &Tp_sel, sizeof(Tp_sel));
+    for (int i = 0; i < n_inst; ++i) {
+        const edm_instance &p = inst[i];
+        work[i] = static_cast<double>(p.N) * p.L * p.L;
+        need[i] = simplex_workspace_bytes(ctx, p.N, p.L, E_max);
+        key = fnv1a(key, &p, sizeof(p));
+        key = fnv1a(key, &E_out[i], sizeof(E_out[i]));
+    }
+    auto fn = [&](edm_ctx *sub, int i) {
+        const edm_instance &p = inst[i];
+        return launch_simplex(sub, p.X, p.N, p.L, E_max, p.tau, Tp_sel, E_out[i], nullptr);
+    };
+    return run_batched(ctx, n_inst, work, need, key, fn);
+}
+
+edm_status edm_set_option(edm_ctx *ctx, const char *name, long long value) {
+    if (!ctx || !name) return EDM_ERR_INVALID_ARG;
+    if (!strcmp(name, "batch_streams") && value >= 1 && value <= 32) {
+        ctx->batch_streams = static_cast<int>(value);
+    } else if (!strcmp(name, "batch_graph") && (value == 0 || value == 1)) {
+        ctx->batch_graph = value != 0;
+    } else if (!strcmp(name, "autotune") && (value == 0 || value == 1)) {
+        ctx->autotune = value != 0;
+    } else if (!strcmp(name, "lookup_libs_per_cta") && value >= 0 && value <= 4096) {
+        ctx->lookup_lb = static_cast<int>(value);
+    } else if (!strcmp(name, "table_budget_mb") && value >= 16) {
+        ctx->table_budget = static_cast<size_t>(value) << 20;
+    } else if (!strcmp(name, "autotune_reset") && value == 1) {
+        ctx->tune->clear();
+    } else {
+        return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_set_option: bad option %s=%lld", name,
+                         value);
+    }
+    ctx->graph_key = 0;  // options change what a captured graph would hold
     return EDM_OK;
 }
 

@@ -6,6 +6,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <map>
 #include <vector>
 
 #include "../../include/edm.h"
@@ -30,6 +31,26 @@ struct edm_ctx {
     cudaEvent_t prof_pending;  // start event of the launch in progress
     std::vector<edm_prof_rec> prof;
     std::vector<cudaEvent_t> prof_pool;
+
+    // options (edm_set_option)
+    int batch_streams = 8;     // concurrent streams of a batched call
+    bool batch_graph = true;   // capture a batched call into a CUDA graph
+    bool autotune = true;      // tune the lookup's libraries per CTA
+    int lookup_lb = 0;         // fixed libraries per CTA (0: tuned or heuristic)
+
+    // autotuner: bucket key -> libraries per CTA (owned by the main context)
+    std::map<uint64_t, int> *tune = nullptr;
+
+    // batched execution: sub-contexts (own stream and workspace), the stream a
+    // graph is captured on and launched from, and the cached graph
+    bool is_sub = false;
+    std::vector<edm_ctx *> subs;
+    cudaStream_t origin = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_done = nullptr;
+    std::vector<cudaEvent_t> ev_join;
+    cudaGraphExec_t graph_exec = nullptr;
+    uint64_t graph_key = 0;
+    uint64_t graph_kernels = 0;  // kernels one replay of graph_exec launches
 };
 
 // device-side error flags, OR-ed into ctx->d_flags
@@ -90,6 +111,9 @@ edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L,
                          const double *ysum, const double *yysum, float *rho, long long rho_ld);
 edm_status launch_smem_probe(edm_ctx *ctx, double ms, double *bytes_per_s);
 size_t simplex_workspace_bytes(edm_ctx *ctx, int N, int L, int E_max);
+// Autotuner bucket of a lookup launch.
+uint64_t lookup_bucket(int L, int N_tgt, int nlib, edm_precision prec);
+int lookup_default_lb(edm_ctx *ctx, int nlib, int n_tiles);
 size_t ccm_slot_bytes(int L, int tau, int Tp);
 size_t target_store_bytes(int N_tgt, int L, edm_precision prec);
 

@@ -444,6 +444,27 @@ __global__ void __launch_bounds__(LkWarps<BF16>::THREADS, 1) lookup_kernel(const
     }
 }
 
+// Heuristic libraries per CTA: enough CTAs for balance (8 per SM), enough
+// libraries per CTA to amortise the target tile load, at most 128.
+int lookup_default_lb(edm_ctx *ctx, int nlib, int n_tiles) {
+    const long long pairs = static_cast<long long>(nlib) * n_tiles;
+    const long long lb = pairs / (8LL * ctx->num_sms);
+    return static_cast<int>(std::max<long long>(1, std::min<long long>(128, lb)));
+}
+
+static int ceil_log2(long long v) {
+    int b = 0;
+    while ((1LL << b) < v) ++b;
+    return b;
+}
+
+uint64_t lookup_bucket(int L, int N_tgt, int nlib, edm_precision prec) {
+    const int tt = targets_per_tile(prec);
+    const int n_tiles = (N_tgt + tt - 1) / tt;
+    return (static_cast<uint64_t>(ceil_log2(L)) << 24) | (static_cast<uint64_t>(ceil_log2(n_tiles)) << 16) |
+           (static_cast<uint64_t>(ceil_log2(nlib)) << 8) | static_cast<uint64_t>(prec);
+}
+
 edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, const uint8_t *tables,
                          size_t slot_bytes, const int32_t *E_lib, int lib0, int nlib, int tau,
                          int Tp, edm_precision prec, const double *ysum, const double *yysum,
@@ -467,11 +488,15 @@ edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, cons
                         static_cast<size_t>(2) * LK_NC * nm * 32 * sizeof(float) +
                         (2 * stages + 5) * sizeof(uint64_t);
 
-    // libraries per CTA: enough CTAs for balance, enough libraries per CTA to
-    // amortise the tile load
-    const long long pairs = static_cast<long long>(nlib) * n_tiles;
-    long long lb = pairs / (8LL * ctx->num_sms);
-    lb = std::max<long long>(1, std::min<long long>(128, lb));
+    // libraries per CTA: a fixed override, else the autotuned value of this
+    // launch's bucket, else the heuristic
+    long long lb = lookup_default_lb(ctx, nlib, n_tiles);
+    if (ctx->lookup_lb > 0) {
+        lb = std::min(ctx->lookup_lb, nlib);
+    } else if (ctx->autotune && ctx->tune) {
+        auto it = ctx->tune->find(lookup_bucket(L, N_tgt, nlib, prec));
+        if (it != ctx->tune->end()) lb = std::min(it->second, nlib);
+    }
     LookupArgs a;
     a.Yt = Yt;
     a.tables = tables;

@@ -72,6 +72,9 @@ def load():
     lib.edm_ccm_all.argtypes = [vp, vp, ci, vp, ci, ci, vp, ci, ci, ci, vp]
     lib.edm_ccm_batched.argtypes = [vp, ctypes.POINTER(edm_instance), ci, ci]
     lib.edm_ccm_window.argtypes = [vp, vp, ci, ci, ci, ci, vp, ci, ci, ci, vp]
+    lib.edm_simplex_optimal_E_batched.argtypes = [vp, ctypes.POINTER(edm_instance), ci, ci, ci,
+                                                  ctypes.POINTER(vp)]
+    lib.edm_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_longlong]
     lib.edm_simplex_optimal_E_noalloc.argtypes = [vp, ci, ci, ci, ci, ci, vp, vp, vp]
     lib.edm_profile_enable.argtypes = [vp, ci]
     lib.edm_profile_read.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
@@ -81,7 +84,8 @@ def load():
     for f in ("edm_create", "edm_destroy", "edm_set_stream", "edm_ctx_sync", "edm_embed",
               "edm_knn", "edm_simplex_optimal_E", "edm_ccm_all", "edm_ccm_batched",
               "edm_profile_enable", "edm_profile_read", "edm_probe_smem_bandwidth",
-              "edm_simplex_optimal_E_noalloc", "edm_ccm_window"):
+              "edm_simplex_optimal_E_noalloc", "edm_ccm_window",
+              "edm_simplex_optimal_E_batched", "edm_set_option"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -264,25 +268,65 @@ def edm_ccm_window(X, offset, L_win, E_lib, tau=1, Tp=0, precision="fp32", out=N
     return rho
 
 
-def edm_ccm_batched(problems, precision="fp32"):
-    """problems: list of dicts with X [N][L], E_lib [N] int32, tau, Tp and
-    optional lib_begin/lib_end; returns the list of rho blocks."""
+def edm_set_option(name, value, device=None):
+    """Set an execution option of the device's context (see include/edm.h)."""
+    dev = device if device is not None else torch.cuda.current_device()
+    ctx = _ctx(dev)
+    _check(ctx, load().edm_set_option(ctx, name.encode(), int(value)), "edm_set_option")
+
+
+def _instances(problems):
     arr = (edm_instance * len(problems))()
-    outs = []
-    device = None
+    keep = []
     for i, p in enumerate(problems):
         X = _series(p["X"], "X", 2)
         N, L = X.shape
-        b, e = p.get("lib_begin", 0), p.get("lib_end", N)
-        rho = torch.empty((e - b, N), dtype=torch.float32, device=X.device)
-        E_lib = p["E_lib"].contiguous()
-        outs.append((rho, X, E_lib))
-        arr[i] = edm_instance(X.data_ptr(), N, L, E_lib.data_ptr(), p.get("tau", 1),
-                              p.get("Tp", 0), rho.data_ptr(), b, e)
-        device = X.device
+        E_lib = p.get("E_lib")
+        E_ptr = 0
+        if E_lib is not None:
+            E_lib = E_lib.contiguous()
+            E_ptr = E_lib.data_ptr()
+        rho = p.get("rho")
+        arr[i] = edm_instance(X.data_ptr(), N, L, E_ptr, p.get("tau", 1), p.get("Tp", 0),
+                              rho.data_ptr() if rho is not None else 0,
+                              p.get("lib_begin", 0), p.get("lib_end", N))
+        keep.append((X, E_lib, rho))
+    return arr, keep
+
+
+def edm_simplex_optimal_E_batched(problems, E_max=EDM_E_MAX, Tp_sel=1):
+    """Optimal E of every series of every problem (dicts with X, tau)."""
     if not problems:
         return []
-    ctx = _ctx(device)
-    _check(ctx, load().edm_ccm_batched(ctx, arr, len(problems), _prec(precision)),
+    arr, keep = _instances(problems)
+    outs = [torch.empty(p["X"].shape[0], dtype=torch.int32, device=p["X"].device)
+            for p in problems]
+    ptrs = (ctypes.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+    ctx = _ctx(problems[0]["X"].device)
+    _check(ctx, load().edm_simplex_optimal_E_batched(ctx, arr, len(problems), E_max, Tp_sel, ptrs),
+           "edm_simplex_optimal_E_batched")
+    return outs
+
+
+def edm_ccm_batched(problems, precision="fp32"):
+    """problems: list of dicts with X [N][L], E_lib [N] int32, tau, Tp, optional
+    lib_begin/lib_end and optional preallocated rho; returns the rho blocks."""
+    if not problems:
+        return []
+    rhos = []
+    probs = []
+    for p in problems:
+        N = p["X"].shape[0]
+        b, e = p.get("lib_begin", 0), p.get("lib_end", N)
+        rho = p.get("rho")
+        if rho is None:
+            rho = torch.empty((e - b, N), dtype=torch.float32, device=p["X"].device)
+        q = dict(p)
+        q["rho"] = rho
+        probs.append(q)
+        rhos.append(rho)
+    arr, keep = _instances(probs)
+    ctx = _ctx(problems[0]["X"].device)
+    _check(ctx, load().edm_ccm_batched(ctx, arr, len(probs), _prec(precision)),
            "edm_ccm_batched")
-    return [o[0] for o in outs]
+    return rhos

@@ -195,3 +195,42 @@ def test_window_convergence_matches_oracle():
     rho = edm.edm_ccm_window(Xg, 200, 500, E_full, 1, 0, "bf16").cpu().numpy()
     ref = oracle.ccm_matrix(X[:, 200:700], X[:, 200:700], E_np, 1, 0, lib_rows=[3])
     assert np.max(np.abs(rho[3] - ref[0])) <= TOL_BF16
+
+
+def _uneven_problems(seed0=300):
+    probs = []
+    for i, (N, L) in enumerate([(40, 240), (96, 900), (33, 2300), (7, 180), (150, 600),
+                                (64, 1500), (12, 3000), (200, 300)]):
+        X = inputs.coupled_logistic(N, L, seed0 + i, 3.6, 3.9, 0.05, 0.1, noise=0.02)
+        probs.append({"X": gpu(X), "tau": 1, "Tp": 0})
+    return probs
+
+
+def test_batched_graph_and_streams_match_single_calls():
+    probs = _uneven_problems()
+    E_list = edm.edm_simplex_optimal_E_batched(probs, 8, 1)
+    for p, E in zip(probs, E_list):
+        ref, _ = edm.edm_simplex_optimal_E(p["X"], 8, 1, 1)
+        torch.testing.assert_close(E, ref, rtol=0, atol=0)
+        p["E_lib"] = E
+    singles = [edm.edm_ccm_all(p["X"], p["X"], p["E_lib"]) for p in probs]
+    for graph in (0, 1):
+        edm.edm_set_option("batch_graph", graph)
+        for _ in range(2):          # the second graph call replays the cached graph
+            outs = edm.edm_ccm_batched(probs)
+            for out, ref in zip(outs, singles):
+                torch.testing.assert_close(out, ref, rtol=0, atol=0, equal_nan=True)
+    edm.edm_set_option("batch_graph", 1)
+    edm.edm_ctx_sync()
+    # and one instance against the oracle
+    X = probs[2]["X"].cpu().numpy()
+    E = probs[2]["E_lib"].cpu().numpy()
+    ref = oracle.ccm_matrix(X, X, E, 1, 0, lib_rows=[0, 32])
+    assert np.max(np.abs(outs[2].cpu().numpy()[[0, 32]] - ref)) <= TOL_FP32
+
+
+def test_set_option_rejects_unknown():
+    with pytest.raises(edm.EdmError):
+        edm.edm_set_option("no_such_option", 1)
+    with pytest.raises(edm.EdmError):
+        edm.edm_set_option("batch_streams", 0)
