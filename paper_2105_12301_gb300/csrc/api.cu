@@ -100,15 +100,26 @@ struct DeviceGuard {
 static bool series_len_ok(int L) { return L >= 2 && L <= EDM_L_MAX; }
 
 // All-to-all CCM of N_lib libraries against N_tgt targets of length L whose
-// rows are ld_lib / ld_tgt floats apart.
+// rows are ld_lib / ld_tgt floats apart.  Libraries are processed in chunks
+// whose neighbour tables fit the table budget; each chunk is grouped by E
+// (launch_group_libs), its tables are built in the grouped layout, then the
+// lookup runs over every (group, target tile).
+static int ccm_chunk(edm_ctx *ctx, int N_lib, size_t slot, int G) {
+    const size_t per = std::max<size_t>(1, ctx->table_budget / slot);
+    return static_cast<int>(std::max<size_t>(1, std::min<size_t>(N_lib, per)));
+}
+
 static size_t ccm_workspace_bytes(edm_ctx *ctx, int N_lib, int N_tgt, int L, int tau, int Tp,
                                   edm_precision prec) {
     const size_t yt_bytes = target_store_bytes(N_tgt, L, prec);
     const size_t mean_bytes = align_up(sizeof(double) * N_tgt, 256);
     const size_t sums_bytes = align_up(sizeof(double) * N_tgt * EDM_E_MAX, 256);
     const size_t slot = ccm_slot_bytes(L, tau, Tp);
-    const size_t chunk = slot ? std::max<size_t>(1, std::min<size_t>(N_lib, ctx->table_budget / slot)) : 1;
-    return yt_bytes + mean_bytes + 2 * sums_bytes + chunk * slot;
+    if (slot == 0) return yt_bytes + mean_bytes + 2 * sums_bytes;
+    const int G = lookup_group(prec);
+    const int chunk = ccm_chunk(ctx, N_lib, slot, G);
+    return yt_bytes + mean_bytes + 2 * sums_bytes + groups_bytes(chunk, G) +
+           static_cast<size_t>(groups_max(chunk, G)) * G * slot;
 }
 
 static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, int N_lib,
@@ -119,8 +130,8 @@ static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, in
     const size_t sums_bytes = align_up(sizeof(double) * N_tgt * EDM_E_MAX, 256);
     const size_t slot = ccm_slot_bytes(L, tau, Tp);
     if (slot == 0) return set_error(ctx, EDM_ERR_INVALID_ARG, "series too short");
-    const int chunk = static_cast<int>(
-        std::max<size_t>(1, std::min<size_t>(N_lib, ctx->table_budget / slot)));
+    const int G = lookup_group(prec);
+    const int chunk = ccm_chunk(ctx, N_lib, slot, G);
     edm_status st = ws_reserve(ctx, ccm_workspace_bytes(ctx, N_lib, N_tgt, L, tau, Tp, prec));
     if (st != EDM_OK) return st;
     uint8_t *base = static_cast<uint8_t *>(ctx->ws);
@@ -128,15 +139,19 @@ static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, in
     double *mean = reinterpret_cast<double *>(base + yt_bytes);
     double *ysum = reinterpret_cast<double *>(base + yt_bytes + mean_bytes);
     double *yysum = reinterpret_cast<double *>(base + yt_bytes + mean_bytes + sums_bytes);
-    uint8_t *tables = base + yt_bytes + mean_bytes + 2 * sums_bytes;
+    uint8_t *gmem = base + yt_bytes + mean_bytes + 2 * sums_bytes;
+    uint8_t *tables = gmem + groups_bytes(chunk, G);
     st = launch_target_store(ctx, Y_tgt, ld_tgt, N_tgt, L, tau, Tp, prec, Yt, mean, ysum, yysum);
     if (st != EDM_OK) return st;
     for (int c0 = 0; c0 < N_lib; c0 += chunk) {
         const int nlib = std::min(chunk, N_lib - c0);
-        st = launch_ccm_tables(ctx, X_lib, ld_lib, c0, nlib, L, E_lib, tau, Tp, tables, slot);
+        const CcmGroups grp = carve_groups(gmem, nlib, G);
+        st = launch_group_libs(ctx, E_lib, c0, nlib, L, tau, Tp, grp);
         if (st != EDM_OK) return st;
-        st = launch_lookup(ctx, Yt, N_tgt, L, tables, slot, E_lib, c0, nlib, tau, Tp, prec, ysum,
-                           yysum, rho + static_cast<size_t>(c0) * N_tgt, N_tgt);
+        st = launch_ccm_tables(ctx, X_lib, ld_lib, nlib, L, tau, Tp, grp, tables);
+        if (st != EDM_OK) return st;
+        st = launch_lookup(ctx, Yt, N_tgt, L, tables, grp, c0, nlib, tau, Tp, prec, ysum, yysum,
+                           rho + static_cast<size_t>(c0) * N_tgt, N_tgt);
         if (st != EDM_OK) return st;
     }
     return EDM_OK;

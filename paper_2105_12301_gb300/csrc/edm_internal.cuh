@@ -88,14 +88,53 @@ __host__ __device__ constexpr int table_pair_bytes(int k) {
     return ((8 * table_row_words(k) + 15) / 16) * 16;
 }
 
+// Libraries of one chunk run in groups of G that share E (hence k, the
+// number of table rows and the first query time), so that the lookup reads
+// each observation row once per group instead of once per library.  A
+// group's tables are interleaved: pair block p of member m sits at byte
+// off + (p * G + m) * table_pair_bytes(E+1).  Libraries whose E is invalid
+// form groups with E = 0 (no tables; their rho rows are NaN).
+// A library can be cross-mapped when 1 <= E <= EDM_E_MAX and its n =
+// L-(E-1)tau-Tp points leave at least E+2 of them (k = E+1 neighbours plus
+// the point itself).
+__host__ __device__ inline bool ccm_E_valid(int E, int L, int tau, int Tp) {
+    return E >= 1 && E <= EDM_E_MAX && L - (E - 1) * tau - Tp >= E + 2;
+}
+
+constexpr int LK_GROUP_FP32 = 4;
+constexpr int LK_GROUP_BF16 = 2;
+inline int lookup_group(edm_precision prec) {
+    return prec == EDM_BF16_TARGETS ? LK_GROUP_BF16 : LK_GROUP_FP32;
+}
+struct CcmGroups {
+    int32_t *E;      // [ngroups_max] E of the members (0: invalid E)
+    int32_t *n;      // [ngroups_max] members, 1..G
+    int32_t *lib;    // [ngroups_max * G] library index; slots n..G-1 of a
+                     // group repeat its first member; -1 past the last group
+    long long *off;  // [ngroups_max] byte offset of the group's tables
+    int32_t *count;  // number of groups (device scalar)
+    int G;
+    int ngroups_max;
+};
+inline int groups_max(int nlib, int G) { return (nlib + G - 1) / G + EDM_E_MAX + 1; }
+// Bytes of the group arrays of a chunk of nlib libraries (see carve_groups).
+size_t groups_bytes(int nlib, int G);
+// Lay the group arrays out in `mem` (groups_bytes(nlib, G) bytes).
+CcmGroups carve_groups(uint8_t *mem, int nlib, int G);
+// Group the libraries lib0 .. lib0+nlib-1 by E (one CTA; order within an E
+// is not specified and does not change any result).
+edm_status launch_group_libs(edm_ctx *ctx, const int32_t *E_lib, int lib0, int nlib, int L,
+                             int tau, int Tp, const CcmGroups &g);
+
 // Launchers (one translation unit each).
 edm_status launch_embed(edm_ctx *ctx, const float *x, int L, int E, int tau, float *out);
 edm_status launch_knn(edm_ctx *ctx, const float *X, int N, int L, int E, int tau, int Tp,
                       int k, int32_t *idx, float *dist);
-// X: library series with row stride ld (>= L) floats.
-edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, long long ld, int lib0, int nlib, int L,
-                             const int32_t *E_lib, int tau, int Tp, uint8_t *tables,
-                             size_t slot_bytes);
+// X: library series with row stride ld (>= L) floats; the libraries are
+// those of the groups g (indexes into X), tables laid out as described at
+// CcmGroups.
+edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, long long ld, int nlib, int L,
+                             int tau, int Tp, const CcmGroups &g, uint8_t *tables);
 edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max, int tau,
                           int Tp_sel, int32_t *E_opt, float *rho_E);
 // Transposed, centred target tiles plus, per E = 1..EDM_E_MAX, the FP64 sums
@@ -105,10 +144,11 @@ edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max,
 edm_status launch_target_store(edm_ctx *ctx, const float *Y, long long ld, int N_tgt, int L,
                                int tau, int Tp, edm_precision prec, uint8_t *Yt, double *mean_ws,
                                double *ysum, double *yysum);
+// rho points at the row of library lib0; row of library i = rho + (i - lib0) * rho_ld.
 edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L,
-                         const uint8_t *tables, size_t slot_bytes, const int32_t *E_lib,
-                         int lib0, int nlib, int tau, int Tp, edm_precision prec,
-                         const double *ysum, const double *yysum, float *rho, long long rho_ld);
+                         const uint8_t *tables, const CcmGroups &g, int lib0, int nlib, int tau,
+                         int Tp, edm_precision prec, const double *ysum, const double *yysum,
+                         float *rho, long long rho_ld);
 edm_status launch_smem_probe(edm_ctx *ctx, double ms, double *bytes_per_s);
 size_t simplex_workspace_bytes(edm_ctx *ctx, int N, int L, int E_max);
 // Autotuner bucket of a lookup launch.

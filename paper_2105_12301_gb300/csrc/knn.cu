@@ -130,8 +130,8 @@ edm_status launch_knn(edm_ctx *ctx, const float *X, int N, int L, int E, int tau
 // table_pair_bytes).  Lane r < K holds neighbour r (time index u) and its
 // normalised weight w.  The warp that writes the last row of an odd table
 // also writes the dummy row that completes its pair.
-__device__ __forceinline__ void write_table_row(uint8_t *slot, int i, int n, int K, int L, int Tp,
-                                                int u, float w) {
+__device__ __forceinline__ void write_table_row(uint8_t *slot, size_t pair_stride, int i, int n,
+                                                int K, int L, int Tp, int u, float w) {
     const int lane = lane_id();
     const int words = table_row_words(K);
     const int h = lane - (K - 1);
@@ -144,7 +144,7 @@ __device__ __forceinline__ void write_table_row(uint8_t *slot, int i, int n, int
         word = static_cast<uint32_t>(ua + Tp) & 0xffffu;
         if (2 * h + 1 < K) word |= (static_cast<uint32_t>(ub + Tp) & 0xffffu) << 16;
     }
-    uint32_t *block = reinterpret_cast<uint32_t *>(slot + static_cast<size_t>(i >> 1) * table_pair_bytes(K));
+    uint32_t *block = reinterpret_cast<uint32_t *>(slot + static_cast<size_t>(i >> 1) * pair_stride);
     if (lane < words) block[2 * lane + (i & 1)] = word;
     if ((n & 1) && i == n - 1 && lane < words)
         block[2 * lane + 1] = lane < K - 1 ? 0u : (static_cast<uint32_t>(L) | (static_cast<uint32_t>(L) << 16));
@@ -154,7 +154,7 @@ __device__ __forceinline__ void write_table_row(uint8_t *slot, int i, int n, int
 // normalised simplex weights, neighbour rows pre-shifted by Tp.
 template <int E>
 __device__ __forceinline__ void table_rows(const float *xs, int L, int tau, int Tp, int r0, int r1,
-                                           WarpScratch *ws, uint8_t *slot) {
+                                           WarpScratch *ws, uint8_t *slot, size_t pair_stride) {
     constexpr int K = E + 1;
     const int lo = (E - 1) * tau, hi = L - 1 - Tp, n = hi - lo + 1;
     const int warp = threadIdx.x >> 5;
@@ -163,37 +163,51 @@ __device__ __forceinline__ void table_rows(const float *xs, int L, int tau, int 
         float d = 0.f;
         knn_row<E, KNN_SET>(xs, lo + i, lo, hi, tau, K, ws, &u, &d);
         const float w = simplex_weight(d, K);
-        write_table_row(slot, i, n, K, L, Tp, u, w);
+        write_table_row(slot, pair_stride, i, n, K, L, Tp, u, w);
     }
 }
 
-__host__ __device__ inline bool ccm_E_valid(int E, int L, int tau, int Tp) {
-    return E >= 1 && E <= EDM_E_MAX && L - (E - 1) * tau - Tp >= E + 2;
+// The library of group slot s (blockIdx.x), its E, where its table starts and
+// the distance between its consecutive pair blocks.  False for an empty slot
+// or a library whose E is invalid (its group has E = 0; the lookup writes its
+// NaN row and raises the flag).
+struct TableSlot {
+    int lib, E;
+    uint8_t *base;
+    size_t pair_stride;
+};
+
+__device__ __forceinline__ bool table_slot(const CcmGroups &g, uint8_t *tables, TableSlot &ts) {
+    const int s = blockIdx.x;
+    ts.lib = g.lib[s];
+    if (ts.lib < 0) return false;
+    const int grp = s / g.G, m = s % g.G;
+    ts.E = g.E[grp];
+    if (ts.E == 0) return false;
+    const size_t pb = table_pair_bytes(ts.E + 1);
+    ts.base = tables + g.off[grp] + m * pb;
+    ts.pair_stride = pb * g.G;
+    return true;
 }
 
 template <bool SMEM>
 __global__ void __launch_bounds__(KNN_WARPS * 32)
-    ccm_table_kernel(const float *__restrict__ X, long long ld, int lib0, int L,
-                     const int32_t *__restrict__ E_lib, int tau, int Tp, int RB,
-                     uint8_t *__restrict__ tables, size_t slot_bytes, int *flags) {
+    ccm_table_kernel(const float *__restrict__ X, long long ld, int L, int tau, int Tp, int RB,
+                     const CcmGroups g, uint8_t *__restrict__ tables) {
     extern __shared__ __align__(16) uint8_t smem[];
     WarpScratch *wsa = reinterpret_cast<WarpScratch *>(smem);
     float *xs_s = reinterpret_cast<float *>(smem + KNN_WARPS * sizeof(WarpScratch));
-    const int lib = lib0 + blockIdx.x;
-    const int E = E_lib[lib];
-    if (!ccm_E_valid(E, L, tau, Tp)) {
-        if (blockIdx.y == 0 && threadIdx.x == 0) set_flag(flags, EDMF_BADARG);
-        return;
-    }
+    TableSlot ts;
+    if (!table_slot(g, tables, ts)) return;
+    const int E = ts.E;
     const int n = L - (E - 1) * tau - Tp;
     const int r0 = blockIdx.y * RB, r1 = min(n, r0 + RB);
     if (r0 >= r1) return;
-    const float *xs = stage_series<SMEM>(X + static_cast<size_t>(lib) * ld, L, xs_s);
+    const float *xs = stage_series<SMEM>(X + static_cast<size_t>(ts.lib) * ld, L, xs_s);
     WarpScratch *ws = wsa + (threadIdx.x >> 5);
-    uint8_t *slot = tables + static_cast<size_t>(blockIdx.x) * slot_bytes;
     switch (E) {
 #define EDM_CASE(e) \
-    case e: table_rows<e>(xs, L, tau, Tp, r0, r1, ws, slot); break;
+    case e: table_rows<e>(xs, L, tau, Tp, r0, r1, ws, ts.base, ts.pair_stride); break;
         EDM_CASE(1) EDM_CASE(2) EDM_CASE(3) EDM_CASE(4) EDM_CASE(5) EDM_CASE(6) EDM_CASE(7)
         EDM_CASE(8) EDM_CASE(9) EDM_CASE(10) EDM_CASE(11) EDM_CASE(12) EDM_CASE(13)
         EDM_CASE(14) EDM_CASE(15) EDM_CASE(16) EDM_CASE(17) EDM_CASE(18) EDM_CASE(19)
@@ -211,28 +225,23 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
 // candidate slot 0 can reach before the start of the series.
 template <int CH, bool HEAD1>
 __global__ void __launch_bounds__(KNN_WARPS * 32)
-    ccm_table_regs_kernel(const float *__restrict__ X, long long ld, int lib0, int L,
-                          const int32_t *__restrict__ E_lib, int tau, int Tp, int RB,
-                          uint8_t *__restrict__ tables, size_t slot_bytes, int *flags) {
+    ccm_table_regs_kernel(const float *__restrict__ X, long long ld, int L, int tau, int Tp,
+                          int RB, const CcmGroups g, uint8_t *__restrict__ tables) {
     extern __shared__ __align__(16) uint8_t smem[];
     WarpScratch *wsa = reinterpret_cast<WarpScratch *>(smem);
     float *xs = reinterpret_cast<float *>(smem + KNN_WARPS * sizeof(WarpScratch));
-    const int lib = lib0 + blockIdx.x;
-    const int E = E_lib[lib];
-    if (!ccm_E_valid(E, L, tau, Tp)) {
-        if (blockIdx.y == 0 && threadIdx.x == 0) set_flag(flags, EDMF_BADARG);
-        return;
-    }
+    TableSlot ts;
+    if (!table_slot(g, tables, ts)) return;
+    const int E = ts.E;
     const int K = E + 1;
     const int lo = (E - 1) * tau, hi = L - 1 - Tp, n = hi - lo + 1;
     const int r0 = blockIdx.y * RB, r1 = min(n, r0 + RB);
     if (r0 >= r1) return;
-    const float *xg = X + static_cast<size_t>(lib) * ld;
+    const float *xg = X + static_cast<size_t>(ts.lib) * ld;
     for (int i = threadIdx.x; i < 32 * CH; i += blockDim.x) xs[i] = i < L ? xg[i] : 0.f;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = lane_id();
     WarpScratch *ws = wsa + warp;
-    uint8_t *slot = tables + static_cast<size_t>(blockIdx.x) * slot_bytes;
     for (int i = r0 + warp; i < r1; i += KNN_WARPS) {
         const int t = lo + i;
         float s[CH];
@@ -256,7 +265,7 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
         float d = 0.f;
         select_set_regs<CH>(s, xs, t, lo, hi, E, tau, K, ws, u, d);
         const float w = simplex_weight(d, K);
-        write_table_row(slot, i, n, K, L, Tp, u, w);
+        write_table_row(ts.base, ts.pair_stride, i, n, K, L, Tp, u, w);
     }
 }
 
@@ -270,12 +279,11 @@ size_t ccm_slot_bytes(int L, int tau, int Tp) {
     return align_up(best, 256);
 }
 
-edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, long long ld, int lib0, int nlib, int L,
-                             const int32_t *E_lib, int tau, int Tp, uint8_t *tables,
-                             size_t slot_bytes) {
+edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, long long ld, int nlib, int L,
+                             int tau, int Tp, const CcmGroups &g, uint8_t *tables) {
     const int n_max = L - Tp;  // rows at E = 1, the most of any E
     const int RB = rows_per_cta(ctx, nlib, n_max);
-    dim3 grid(nlib, (n_max + RB - 1) / RB);
+    dim3 grid(g.ngroups_max * g.G, (n_max + RB - 1) / RB);
     const int ch = (L + 31) / 32;
     if (ch <= 64) {
         const int CHs[] = {8, 16, 24, 32, 48, 64};
@@ -283,8 +291,8 @@ edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, long long ld, int lib
         for (int c : CHs)
             if (c >= ch) { CH = c; break; }
         const bool head1 = (EDM_E_MAX - 1) * tau < 32;
-        void (*kern)(const float *, long long, int, int, const int32_t *, int, int, int, uint8_t *,
-                     size_t, int *) = nullptr;
+        void (*kern)(const float *, long long, int, int, int, int, const CcmGroups, uint8_t *) =
+            nullptr;
         switch (CH) {
         case 8: kern = head1 ? ccm_table_regs_kernel<8, true> : ccm_table_regs_kernel<8, false>; break;
         case 16: kern = head1 ? ccm_table_regs_kernel<16, true> : ccm_table_regs_kernel<16, false>; break;
@@ -296,8 +304,7 @@ edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, long long ld, int lib
         const size_t smem = KNN_WARPS * sizeof(WarpScratch) + sizeof(float) * 32 * CH;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         before_launch(ctx);
-        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, lib0, L, E_lib, tau, Tp, RB, tables,
-                                                          slot_bytes, ctx->d_flags);
+        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, L, tau, Tp, RB, g, tables);
         return after_launch(ctx, "ccm_table_kernel");
     }
     const bool smem_series = sizeof(float) * static_cast<size_t>(L) <= SERIES_SMEM_MAX;
@@ -306,16 +313,110 @@ edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, long long ld, int lib
         auto kern = ccm_table_kernel<true>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         before_launch(ctx);
-        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, lib0, L, E_lib, tau, Tp, RB, tables,
-                                                          slot_bytes, ctx->d_flags);
+        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, L, tau, Tp, RB, g, tables);
     } else {
         auto kern = ccm_table_kernel<false>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         before_launch(ctx);
-        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, lib0, L, E_lib, tau, Tp, RB, tables,
-                                                          slot_bytes, ctx->d_flags);
+        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, L, tau, Tp, RB, g, tables);
     }
     return after_launch(ctx, "ccm_table_kernel");
+}
+
+// ------------------------------------------------------ grouping by E
+
+size_t groups_bytes(int nlib, int G) {
+    const size_t ng = static_cast<size_t>(groups_max(nlib, G));
+    return 3 * align_up(4 * ng, 256) + align_up(8 * ng, 256) + align_up(4 * ng * G, 256) + 256;
+}
+
+CcmGroups carve_groups(uint8_t *mem, int nlib, int G) {
+    const size_t ng = static_cast<size_t>(groups_max(nlib, G));
+    CcmGroups g;
+    g.G = G;
+    g.ngroups_max = static_cast<int>(ng);
+    g.off = reinterpret_cast<long long *>(mem);
+    mem += align_up(8 * ng, 256);
+    g.E = reinterpret_cast<int32_t *>(mem);
+    mem += align_up(4 * ng, 256);
+    g.n = reinterpret_cast<int32_t *>(mem);
+    mem += align_up(4 * ng, 256);
+    g.lib = reinterpret_cast<int32_t *>(mem);
+    mem += align_up(4 * ng * G, 256);
+    g.count = reinterpret_cast<int32_t *>(mem);
+    return g;
+}
+
+constexpr int GROUP_THREADS = 1024;
+
+// One CTA: histogram of E (bucket 0 for an invalid E), then groups of G per
+// bucket in bucket order with the byte offsets of their tables, then every
+// library placed in a slot of its bucket's groups.
+__global__ void __launch_bounds__(GROUP_THREADS)
+    group_libs_kernel(const int32_t *__restrict__ E_lib, int lib0, int nlib, int L, int tau,
+                      int Tp, const CcmGroups g) {
+    __shared__ int cnt[EDM_E_MAX + 1], fill[EDM_E_MAX + 1], gbase[EDM_E_MAX + 2];
+    __shared__ long long obase[EDM_E_MAX + 1], gbytes[EDM_E_MAX + 1];
+    const int tid = threadIdx.x, G = g.G;
+    if (tid <= EDM_E_MAX) {
+        cnt[tid] = 0;
+        fill[tid] = 0;
+    }
+    for (int s = tid; s < g.ngroups_max * G; s += GROUP_THREADS) g.lib[s] = -1;
+    __syncthreads();
+    for (int i = tid; i < nlib; i += GROUP_THREADS) {
+        const int E = E_lib[lib0 + i];
+        atomicAdd(&cnt[ccm_E_valid(E, L, tau, Tp) ? E : 0], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int ng = 0;
+        long long off = 0;
+        for (int b = 0; b <= EDM_E_MAX; ++b) {
+            const int groups = (cnt[b] + G - 1) / G;
+            const long long npairs = b ? (L - (b - 1) * tau - Tp + 1) / 2 : 0;
+            gbase[b] = ng;
+            obase[b] = off;
+            gbytes[b] = npairs * G * table_pair_bytes(b + 1);
+            ng += groups;
+            off += groups * gbytes[b];
+        }
+        gbase[EDM_E_MAX + 1] = ng;
+        *g.count = ng;
+    }
+    __syncthreads();
+    const int ng = gbase[EDM_E_MAX + 1];
+    for (int gi = tid; gi < ng; gi += GROUP_THREADS) {
+        int b = 0;
+        while (gbase[b + 1] <= gi) ++b;  // gbase is nondecreasing; gi < gbase[E_MAX+1]
+        const int j = gi - gbase[b];
+        g.E[gi] = b;
+        g.n[gi] = min(G, cnt[b] - j * G);
+        g.off[gi] = obase[b] + j * gbytes[b];
+    }
+    for (int i = tid; i < nlib; i += GROUP_THREADS) {
+        const int E = E_lib[lib0 + i];
+        const int b = ccm_E_valid(E, L, tau, Tp) ? E : 0;
+        const int pos = atomicAdd(&fill[b], 1);
+        g.lib[(gbase[b] + pos / G) * G + pos % G] = lib0 + i;
+    }
+    __syncthreads();
+    // the empty slots of a partial group repeat its first member: their
+    // tables are built and gathered like the others (the lookup then needs no
+    // per-member test) and their results are never written
+    for (int gi = tid; gi < ng; gi += GROUP_THREADS) {
+        int b = 0;
+        while (gbase[b + 1] <= gi) ++b;
+        const int nm = min(G, cnt[b] - (gi - gbase[b]) * G);
+        for (int m = nm; m < G; ++m) g.lib[gi * G + m] = g.lib[gi * G];
+    }
+}
+
+edm_status launch_group_libs(edm_ctx *ctx, const int32_t *E_lib, int lib0, int nlib, int L,
+                             int tau, int Tp, const CcmGroups &g) {
+    before_launch(ctx);
+    group_libs_kernel<<<1, GROUP_THREADS, 0, ctx->stream>>>(E_lib, lib0, nlib, L, tau, Tp, g);
+    return after_launch(ctx, "group_libs_kernel");
 }
 
 }  // namespace edm

@@ -352,14 +352,47 @@ template <int CH>
 __device__ __forceinline__ void select_set_regs(const float (&s)[CH], const float *xs, int t,
                                                 int lo, int hi, int E, int tau, int K,
                                                 WarpScratch *ws, int &u_out, float &d_out) {
+    static_assert(CH % 4 == 0, "slots come in groups of four");
+    constexpr int NG = CH / 4;
     const int lane = lane_id();
     const int nc = hi - lo;
     const int R = min(K + 1, nc);
+    // minima of the slot groups (4 slots each) and of the lane
+    float gm[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+        gm[g] = fminf(fminf(s[4 * g], s[4 * g + 1]), fminf(s[4 * g + 2], s[4 * g + 3]));
     float lmin = EDM_INF;
 #pragma unroll
-    for (int j = 0; j < CH; ++j) lmin = fminf(lmin, s[j]);
+    for (int g = 0; g < NG; ++g) lmin = fminf(lmin, gm[g]);
     const float theta = warp_sorted_at_f(lmin, R - 1);
-    int c = compact_le<CH>(s, theta, ws);
+    int c;
+    if (theta == EDM_INF) {
+        c = compact_le<CH>(s, theta, ws);
+    } else {
+        // theta is finite, so s <= theta excludes the +inf non-candidates;
+        // only slot groups in which some lane holds such a value are visited
+        const unsigned lt = (1u << lane) - 1u;
+        int base = 0;
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+            if (__any_sync(FULL, gm[g] <= theta)) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int j = 4 * g + i;
+                    const bool p = s[j] <= theta;
+                    const unsigned b = __ballot_sync(FULL, p);
+                    if (p) {
+                        const int pos = base + __popc(b & lt);
+                        if (pos < KNN_CAP) ws->key[pos] = mk_key(s[j], lane + 32 * j);
+                    }
+                    base += __popc(b);
+                }
+            }
+        }
+        __syncwarp();
+        c = base;
+    }
     if (c <= KNN_CAP) {
         rank_keys(ws, c, R);
         const float edge = band_edge(key_s(ws->sel[K - 1]), E);

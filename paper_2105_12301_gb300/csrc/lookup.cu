@@ -4,33 +4,41 @@
 // Targets are first stored transposed and centred, in tiles of 32 (FP32) or
 // 64 (BF16) targets: Yt[tile][u][lane], one 128-byte row per time u.  One
 // CTA owns one target tile (staged in shared memory by a bulk TMA copy) and
-// a block of libraries.  A producer warp streams the libraries' neighbour
-// tables through a ring of shared-memory stages (bulk TMA copies completing
-// on mbarriers); sixteen consumer warps take one table row (one query time)
-// at a time: the k (neighbour row, weight) pairs are warp-uniform broadcast
-// reads (one 16-byte read for k <= 3), and lane l gathers target l's value
-// at each neighbour row -- all 32 lanes read one 128-byte shared-memory row,
-// so every gather is a single conflict-free wavefront.  The prediction never
-// leaves registers; each lane accumulates the prediction's sum, its sum of
-// squares and its cross product with the observation in FP32.  The target's
-// own sums over the observation window are precomputed in FP64 per (target,
-// E).  A finisher warp adds the consumers' partials and forms rho in FP64,
-// handed over through a pair of mbarriers so that no consumer waits for it.
+// a block of library groups (libraries of equal E, see CcmGroups).  A
+// producer warp streams the groups' interleaved neighbour tables through a
+// ring of shared-memory stages (bulk TMA copies completing on mbarriers);
+// sixteen consumer warps take one pair of query times at a time: they read
+// the two observations once, then, for every member library, the pair's
+// (neighbour row, weight) values as warp-uniform broadcast reads, and lane l
+// gathers target l's value at each neighbour row -- all 32 lanes read one
+// 128-byte shared-memory row, so every gather is a single conflict-free
+// wavefront.  The prediction never leaves registers; each lane accumulates
+// the prediction's sum, its sum of squares and its cross product with the
+// observation in FP32, per member.  The target's own sums over the
+// observation window are precomputed in FP64 per (target, E).  At the end of
+// a group, consumer warp w+8 hands its partial moments to warp w, which adds
+// them to its own and passes the sum on; a finisher warp adds those eight
+// and forms rho in FP64 (a fixed summation order, handed over through
+// mbarriers).
 #include <cuda_bf16.h>
 
 #include "edm_internal.cuh"
 
 namespace edm {
 
-// consumer warps: 24 with FP32 targets, 16 with BF16 (whose six moments
-// per lane need a larger hand-over buffer next to the tile)
-template <bool BF16> struct LkWarps {
-    static constexpr int NC = BF16 ? 16 : 24;
-    static constexpr int PRODUCER = NC;       // warp issuing the bulk copies
-    static constexpr int FINISHER = NC + 1;   // warp turning moments into rho
+// Warp roles of the lookup CTA; G libraries per group, NM FP32 moments per
+// lane and library (3 per target: sum of the prediction, of its square and
+// of its product with the observation).
+template <bool BF16> struct LkCfg {
+    static constexpr int NC = 16;                  // consumer warps
+    static constexpr int G = BF16 ? LK_GROUP_BF16 : LK_GROUP_FP32;
+    static constexpr int NM = BF16 ? 6 : 3;
+    static constexpr int PRODUCER = NC;            // warp issuing the bulk copies
+    static constexpr int FINISHER = NC + 1;        // warp turning moments into rho
     static constexpr int THREADS = (NC + 2) * 32;
+    static constexpr int HALF = NC / 2;            // hand-over slots
+    static constexpr int RED_FLOATS = HALF * G * NM * 32;  // hand-over buffer
 };
-constexpr int LK_STAGE_BYTES = 6144;           // table bytes per pipeline stage
 constexpr int LK_MAX_STAGES = 8;
 constexpr int LK_TILE_ROW = 128;               // bytes per time row of a tile
 
@@ -172,33 +180,21 @@ edm_status launch_target_store(edm_ctx *ctx, const float *Y, long long ld, int N
 struct LookupArgs {
     const uint8_t *Yt;
     const uint8_t *tables;
-    size_t slot_bytes;
-    const int32_t *E_lib;  // indexed by library id
+    CcmGroups grp;
     const double *ysum;    // [EDM_E_MAX][N_tgt]
     const double *yysum;
-    int lib0, nlib, LB;    // libraries [lib0, lib0+nlib) of this launch; LB per CTA
+    int lib0, GB;          // rho row 0 is library lib0; GB groups per CTA
     int L, tau, Tp, N_tgt;
-    int stages;
-    float *rho;            // row of library lib0
+    int stages, stage_bytes;
+    float *rho;
     long long rho_ld;
     int *flags;
 };
 
-__device__ __forceinline__ bool lib_valid(int E, int L, int tau, int Tp) {
-    return E >= 1 && E <= EDM_E_MAX && L - (E - 1) * tau - Tp >= E + 2;
-}
-
-// Row pairs of one table chunk: as many whole pair blocks as fit a stage.
-__host__ __device__ constexpr int chunk_pairs(int K) { return LK_STAGE_BYTES / table_pair_bytes(K); }
-
-template <bool BF16>
-struct Moments {
-    static constexpr int N = BF16 ? 6 : 3;  // per target: sum a, sum a^2, sum a*b
-};
-
-// Per-lane prediction moments: for each of the lane's targets, the sums of
-// the prediction, of its square and of its product with the observation,
-// kept as (row 2p, row 2p+1) pairs for the packed FP32x2 arithmetic.
+// Per-lane prediction moments of one library: for each of the lane's
+// targets, the sums of the prediction, of its square and of its product with
+// the observation, kept as (row 2p, row 2p+1) pairs for the packed FP32x2
+// arithmetic.
 template <bool BF16>
 struct PairMoments {
     static constexpr int T = BF16 ? 2 : 1;  // targets per lane
@@ -207,14 +203,16 @@ struct PairMoments {
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
-// One table pair block (query times 2p and 2p+1) for this lane's target(s).
-// For each row the prediction is y_last + sum_q w_q (y_q - y_last) over its
-// K neighbour rows (the K-th weight is 1 minus the others); the two rows run
-// side by side in FFMA2/FADD2 lanes.  y_q - y_last is formed as
-// fma(y_last, -1, y_q): the exact difference rounded once, as a subtraction.
+// One table pair block (query times 2p and 2p+1) of one library for this
+// lane's target(s); yA / yB are the lane's stored observation words of the
+// two times.  For each row the prediction is y_last + sum_q w_q (y_q -
+// y_last) over its K neighbour rows (the K-th weight is 1 minus the others);
+// the two rows run side by side in FFMA2/FADD2 lanes.  y_q - y_last is formed
+// as fma(y_last, -1, y_q): the exact difference rounded once, as a
+// subtraction.
 template <int K, bool BF16, bool SMEM_TILE>
-__device__ __forceinline__ void lookup_pair(const uint8_t *blk, const uint32_t *tl, int yrow,
-                                            PairMoments<BF16> &m) {
+__device__ __forceinline__ void lookup_pair(const uint8_t *blk, const uint32_t *tl, uint32_t yA,
+                                            uint32_t yB, PairMoments<BF16> &m) {
     constexpr int PB = table_pair_bytes(K);
     constexpr int NV = PB / 16;
     uint32_t wd[4 * NV];
@@ -235,8 +233,6 @@ __device__ __forceinline__ void lookup_pair(const uint8_t *blk, const uint32_t *
         gA[q] = SMEM_TILE ? tl[uA * 32] : __ldg(tl + uA * 32);
         gB[q] = SMEM_TILE ? tl[uB * 32] : __ldg(tl + uB * 32);
     }
-    const uint32_t yA = SMEM_TILE ? tl[yrow * 32] : __ldg(tl + yrow * 32);
-    const uint32_t yB = SMEM_TILE ? tl[(yrow + 1) * 32] : __ldg(tl + (yrow + 1) * 32);
     const float2 m1 = f2(-1.f, -1.f);
 #pragma unroll
     for (int c = 0; c < PairMoments<BF16>::T; ++c) {
@@ -259,16 +255,19 @@ __device__ __forceinline__ void lookup_pair(const uint8_t *blk, const uint32_t *
     }
 }
 
-// Gather + accumulate one library whose k = K is a compile-time value.
-// Warps take pair blocks warp, warp + NC, ... of each chunk.
+// Gather + accumulate one group whose k = K is a compile-time value: warps
+// take pairs warp, warp + NC, ... of each stage; a pair's observations are
+// read once and serve every member of the group.  All G slots are processed
+// (the empty slots of a partial group hold a copy of its first member).
 template <int K, bool BF16, bool SMEM_TILE>
-__device__ __forceinline__ void consume_library(const LookupArgs &a, const uint8_t *tile,
-                                                const uint8_t *stages, uint64_t *full,
-                                                uint64_t *empty, int &seq, int n, int t0,
-                                                PairMoments<BF16> &m) {
+__device__ __forceinline__ void consume_group(const LookupArgs &a, const uint8_t *tile,
+                                              const uint8_t *stages, uint64_t *full,
+                                              uint64_t *empty, int &seq, int n, int t0,
+                                              PairMoments<BF16> (&pm)[LkCfg<BF16>::G]) {
+    using C = LkCfg<BF16>;
     constexpr int PB = table_pair_bytes(K);
-    constexpr int CP = LK_STAGE_BYTES / PB;
-    constexpr int LK_NC = LkWarps<BF16>::NC;
+    constexpr int GPB = C::G * PB;
+    const int CP = a.stage_bytes / GPB;
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const uint32_t *tl = reinterpret_cast<const uint32_t *>(tile) + lane;
     const int npairs = (n + 1) >> 1;
@@ -276,11 +275,18 @@ __device__ __forceinline__ void consume_library(const LookupArgs &a, const uint8
         const int s = seq % a.stages;
         const uint32_t par = (seq / a.stages) & 1;
         mbar_wait_bounded(&full[s], par, a.flags);
-        const uint8_t *st = stages + static_cast<size_t>(s) * LK_STAGE_BYTES;
+        const uint8_t *st = stages + static_cast<size_t>(s) * a.stage_bytes;
         const int pairs = min(CP, npairs - p0);
         const int ybase = t0 + a.Tp + 2 * p0;
-        for (int p = warp; p < pairs; p += LK_NC)
-            lookup_pair<K, BF16, SMEM_TILE>(st + p * PB, tl, ybase + 2 * p, m);
+        for (int p = warp; p < pairs; p += C::NC) {
+            const int yrow = ybase + 2 * p;
+            const uint32_t yA = SMEM_TILE ? tl[yrow * 32] : __ldg(tl + yrow * 32);
+            const uint32_t yB = SMEM_TILE ? tl[(yrow + 1) * 32] : __ldg(tl + (yrow + 1) * 32);
+            const uint8_t *blk = st + static_cast<size_t>(p) * GPB;
+#pragma unroll
+            for (int m = 0; m < C::G; ++m)
+                lookup_pair<K, BF16, SMEM_TILE>(blk + m * PB, tl, yA, yB, pm[m]);
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         ++seq;
@@ -295,41 +301,39 @@ __device__ __forceinline__ float finish_rho(double n, double sa, double saa, dou
 }
 
 template <bool BF16, bool SMEM_TILE>
-__global__ void __launch_bounds__(LkWarps<BF16>::THREADS, 1) lookup_kernel(const LookupArgs a) {
+__global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const LookupArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
-    constexpr int NM = Moments<BF16>::N;
-    constexpr int LK_NC = LkWarps<BF16>::NC;
-    constexpr int LK_PRODUCER = LkWarps<BF16>::PRODUCER;
-    constexpr int LK_FINISHER = LkWarps<BF16>::FINISHER;
+    using C = LkCfg<BF16>;
     constexpr int TT = BF16 ? 64 : 32;
+    constexpr int G = C::G, NM = C::NM;
+    const int g0 = blockIdx.y * a.GB;
+    const int g1 = min(*a.grp.count, g0 + a.GB);
+    if (g0 >= g1) return;  // every thread of the CTA leaves here together
     const int tile_id = blockIdx.x;
-    const int lb0 = a.lib0 + blockIdx.y * a.LB;
-    const int lb1 = min(a.lib0 + a.nlib, lb0 + a.LB);
     const size_t tile_bytes = static_cast<size_t>(a.L + 1) * LK_TILE_ROW;
     const uint8_t *tile_g = a.Yt + static_cast<size_t>(tile_id) * tile_bytes;
     uint8_t *tile_s = smem;
     uint8_t *stages = smem + (SMEM_TILE ? tile_bytes : 0);
-    float *red = reinterpret_cast<float *>(stages + static_cast<size_t>(a.stages) * LK_STAGE_BYTES);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(red + 2 * LK_NC * NM * 32);
+    float *red = reinterpret_cast<float *>(stages + static_cast<size_t>(a.stages) * a.stage_bytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(red + C::RED_FLOATS);
     uint64_t *full = bars, *empty = bars + a.stages, *tbar = bars + 2 * a.stages;
-    uint64_t *red_full = tbar + 1, *red_empty = tbar + 3;
+    uint64_t *red_full = tbar + 1, *red_empty = tbar + 2, *half_full = tbar + 3;
     const int warp = threadIdx.x >> 5, lane = lane_id();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < a.stages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], LK_NC);
+            mbar_init(&empty[s], C::NC);
         }
         mbar_init(tbar, 1);
-        for (int p = 0; p < 2; ++p) {
-            mbar_init(&red_full[p], LK_NC);
-            mbar_init(&red_empty[p], 1);
-        }
+        mbar_init(red_full, C::HALF);
+        mbar_init(red_empty, 1);
+        mbar_init(half_full, C::NC - C::HALF);
         fence_barrier_init();
     }
     __syncthreads();
 
-    if (warp == LK_PRODUCER) {
+    if (warp == C::PRODUCER) {
         // ---------------- producer: target tile, then the table stream
         if (lane == 0) {
             if (SMEM_TILE) {
@@ -340,21 +344,21 @@ __global__ void __launch_bounds__(LkWarps<BF16>::THREADS, 1) lookup_kernel(const
                                   tbar);
             }
             int seq = 0;
-            for (int lib = lb0; lib < lb1; ++lib) {
-                const int E = a.E_lib[lib];
-                if (!lib_valid(E, a.L, a.tau, a.Tp)) continue;
+            for (int gi = g0; gi < g1; ++gi) {
+                const int E = a.grp.E[gi];
+                if (E == 0) continue;
                 const int n = a.L - (E - 1) * a.tau - a.Tp;
                 const int npairs = (n + 1) >> 1;
-                const int PB = table_pair_bytes(E + 1);
-                const int CP = chunk_pairs(E + 1);
-                const uint8_t *slot = a.tables + static_cast<size_t>(lib - a.lib0) * a.slot_bytes;
+                const int GPB = G * table_pair_bytes(E + 1);
+                const int CP = a.stage_bytes / GPB;
+                const uint8_t *src = a.tables + a.grp.off[gi];
                 for (int p0 = 0; p0 < npairs; p0 += CP) {
                     const int s = seq % a.stages, j = seq / a.stages;
                     if (j > 0) mbar_wait_bounded(&empty[s], (j - 1) & 1, a.flags);
-                    const uint32_t bytes = static_cast<uint32_t>(min(CP, npairs - p0) * PB);
+                    const uint32_t bytes = static_cast<uint32_t>(min(CP, npairs - p0) * GPB);
                     mbar_arrive_expect_tx(&full[s], bytes);
-                    bulk_copy_g2s(stages + static_cast<size_t>(s) * LK_STAGE_BYTES,
-                                  slot + static_cast<size_t>(p0) * PB, bytes, &full[s]);
+                    bulk_copy_g2s(stages + static_cast<size_t>(s) * a.stage_bytes,
+                                  src + static_cast<size_t>(p0) * GPB, bytes, &full[s]);
                     ++seq;
                 }
             }
@@ -362,44 +366,57 @@ __global__ void __launch_bounds__(LkWarps<BF16>::THREADS, 1) lookup_kernel(const
         return;
     }
 
-    if (warp == LK_FINISHER) {
-        // ---------------- finisher: rho of every library of this CTA
+    if (warp == C::FINISHER) {
+        // ---------------- finisher: rho of every member of every group
         int done = 0;
-        for (int lib = lb0; lib < lb1; ++lib) {
-            const int E = a.E_lib[lib];
-            float *rho_row = a.rho + static_cast<long long>(lib - a.lib0) * a.rho_ld;
-            if (!lib_valid(E, a.L, a.tau, a.Tp)) {
-                for (int j = lane; j < TT; j += 32) {
-                    const int tgt = tile_id * TT + j;
-                    if (tgt < a.N_tgt) rho_row[tgt] = __int_as_float(0x7fc00000);
+        for (int gi = g0; gi < g1; ++gi) {
+            const int E = a.grp.E[gi], nm = a.grp.n[gi];
+            const int32_t *libs = a.grp.lib + static_cast<size_t>(gi) * G;
+            if (E == 0) {
+                for (int m = 0; m < nm; ++m) {
+                    float *rho_row = a.rho + static_cast<long long>(libs[m] - a.lib0) * a.rho_ld;
+                    for (int j = lane; j < TT; j += 32) {
+                        const int tgt = tile_id * TT + j;
+                        if (tgt < a.N_tgt) rho_row[tgt] = __int_as_float(0x7fc00000);
+                    }
                 }
                 if (lane == 0 && blockIdx.x == 0) set_flag(a.flags, EDMF_BADARG);
                 continue;
             }
-            const int p = done & 1;
-            mbar_wait_bounded(&red_full[p], (done >> 1) & 1, a.flags);
-            const float *base = red + p * LK_NC * NM * 32;
-            float S[NM];
+            mbar_wait_bounded(red_full, done & 1, a.flags);
+            float S[G][NM];
 #pragma unroll
-            for (int j = 0; j < NM; ++j) S[j] = 0.f;
-            for (int w = 0; w < LK_NC; ++w)
+            for (int m = 0; m < G; ++m)
 #pragma unroll
-                for (int j = 0; j < NM; ++j) S[j] += base[(w * NM + j) * 32 + lane];
+                for (int j = 0; j < NM; ++j) S[m][j] = 0.f;
+            for (int w = 0; w < C::HALF; ++w)
+#pragma unroll
+                for (int m = 0; m < G; ++m)
+                    if (m < nm)
+#pragma unroll
+                        for (int j = 0; j < NM; ++j) S[m][j] += red[((w * G + m) * NM + j) * 32 + lane];
             __syncwarp();
-            if (lane == 0) mbar_arrive(&red_empty[p]);
+            if (lane == 0) mbar_arrive(red_empty);
             const double dn = static_cast<double>(a.L - (E - 1) * a.tau - a.Tp);
             const size_t wo = static_cast<size_t>(E - 1) * a.N_tgt;
-            if (!BF16) {
-                const int tgt = tile_id * 32 + lane;
-                if (tgt < a.N_tgt)
-                    rho_row[tgt] = finish_rho(dn, S[0], S[1], S[2], a.ysum[wo + tgt], a.yysum[wo + tgt]);
-            } else {
-                const int tgt = tile_id * 64 + 2 * lane;
-                if (tgt < a.N_tgt)
-                    rho_row[tgt] = finish_rho(dn, S[0], S[1], S[2], a.ysum[wo + tgt], a.yysum[wo + tgt]);
-                if (tgt + 1 < a.N_tgt)
-                    rho_row[tgt + 1] = finish_rho(dn, S[3], S[4], S[5], a.ysum[wo + tgt + 1],
-                                                  a.yysum[wo + tgt + 1]);
+#pragma unroll
+            for (int m = 0; m < G; ++m) {
+                if (m >= nm) continue;
+                float *rho_row = a.rho + static_cast<long long>(libs[m] - a.lib0) * a.rho_ld;
+                if (!BF16) {
+                    const int tgt = tile_id * 32 + lane;
+                    if (tgt < a.N_tgt)
+                        rho_row[tgt] = finish_rho(dn, S[m][0], S[m][1], S[m][2], a.ysum[wo + tgt],
+                                                  a.yysum[wo + tgt]);
+                } else {
+                    const int tgt = tile_id * 64 + 2 * lane;
+                    if (tgt < a.N_tgt)
+                        rho_row[tgt] = finish_rho(dn, S[m][0], S[m][1], S[m][2], a.ysum[wo + tgt],
+                                                  a.yysum[wo + tgt]);
+                    if (tgt + 1 < a.N_tgt)
+                        rho_row[tgt + 1] = finish_rho(dn, S[m][3], S[m][4], S[m][5],
+                                                      a.ysum[wo + tgt + 1], a.yysum[wo + tgt + 1]);
+                }
             }
             ++done;
         }
@@ -410,17 +427,20 @@ __global__ void __launch_bounds__(LkWarps<BF16>::THREADS, 1) lookup_kernel(const
     const uint8_t *tile = SMEM_TILE ? tile_s : tile_g;
     if (SMEM_TILE) mbar_wait_bounded(tbar, 0, a.flags);
     int seq = 0, done = 0;
-    PairMoments<BF16> pm;
-    for (int lib = lb0; lib < lb1; ++lib) {
-        const int E = a.E_lib[lib];
-        if (!lib_valid(E, a.L, a.tau, a.Tp)) continue;
+    PairMoments<BF16> pm[G];
+    for (int gi = g0; gi < g1; ++gi) {
+        const int E = a.grp.E[gi];
+        if (E == 0) continue;
+        const int nm = a.grp.n[gi];
         const int n = a.L - (E - 1) * a.tau - a.Tp, t0 = (E - 1) * a.tau;
 #pragma unroll
-        for (int c = 0; c < PairMoments<BF16>::T; ++c)
-            pm.s[c] = pm.ss[c] = pm.sy[c] = f2(0.f, 0.f);
+        for (int m = 0; m < G; ++m)
+#pragma unroll
+            for (int c = 0; c < PairMoments<BF16>::T; ++c)
+                pm[m].s[c] = pm[m].ss[c] = pm[m].sy[c] = f2(0.f, 0.f);
         switch (E + 1) {
 #define EDM_CASE(k) \
-    case k: consume_library<k, BF16, SMEM_TILE>(a, tile, stages, full, empty, seq, n, t0, pm); break;
+    case k: consume_group<k, BF16, SMEM_TILE>(a, tile, stages, full, empty, seq, n, t0, pm); break;
             EDM_CASE(2) EDM_CASE(3) EDM_CASE(4) EDM_CASE(5) EDM_CASE(6) EDM_CASE(7) EDM_CASE(8)
             EDM_CASE(9) EDM_CASE(10) EDM_CASE(11) EDM_CASE(12) EDM_CASE(13) EDM_CASE(14)
             EDM_CASE(15) EDM_CASE(16) EDM_CASE(17) EDM_CASE(18) EDM_CASE(19) EDM_CASE(20)
@@ -428,18 +448,38 @@ __global__ void __launch_bounds__(LkWarps<BF16>::THREADS, 1) lookup_kernel(const
 #undef EDM_CASE
         default: break;
         }
-        // hand the partial moments to the finisher (double-buffered)
-        const int p = done & 1;
-        if (done >= 2) mbar_wait_bounded(&red_empty[p], ((done >> 1) - 1) & 1, a.flags);
-        float *rb = red + (p * LK_NC + warp) * NM * 32;
+        // hand the partial moments on (one buffer of HALF slots): warp w+HALF
+        // writes slot w once the finisher has read the previous group; warp w
+        // adds slot w to its own partials, writes the sum back and signals
+        // the finisher
+        const bool upper = warp >= C::HALF;
+        float *rb0 = red + (upper ? warp - C::HALF : warp) * G * NM * 32;
+        if (upper) {
+            if (done > 0) mbar_wait_bounded(red_empty, (done - 1) & 1, a.flags);
+        } else {
+            mbar_wait_bounded(half_full, done & 1, a.flags);
+        }
 #pragma unroll
-        for (int c = 0; c < PairMoments<BF16>::T; ++c) {
-            rb[(3 * c + 0) * 32 + lane] = pm.s[c].x + pm.s[c].y;
-            rb[(3 * c + 1) * 32 + lane] = pm.ss[c].x + pm.ss[c].y;
-            rb[(3 * c + 2) * 32 + lane] = pm.sy[c].x + pm.sy[c].y;
+        for (int m = 0; m < G; ++m) {
+            if (m >= nm) continue;
+            float *rb = rb0 + m * NM * 32;
+#pragma unroll
+            for (int c = 0; c < PairMoments<BF16>::T; ++c) {
+                float v0 = pm[m].s[c].x + pm[m].s[c].y;
+                float v1 = pm[m].ss[c].x + pm[m].ss[c].y;
+                float v2 = pm[m].sy[c].x + pm[m].sy[c].y;
+                if (!upper) {
+                    v0 += rb[(3 * c + 0) * 32 + lane];
+                    v1 += rb[(3 * c + 1) * 32 + lane];
+                    v2 += rb[(3 * c + 2) * 32 + lane];
+                }
+                rb[(3 * c + 0) * 32 + lane] = v0;
+                rb[(3 * c + 1) * 32 + lane] = v1;
+                rb[(3 * c + 2) * 32 + lane] = v2;
+            }
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&red_full[p]);
+        if (lane == 0) mbar_arrive(upper ? half_full : red_full);
         ++done;
     }
 }
@@ -466,30 +506,32 @@ uint64_t lookup_bucket(int L, int N_tgt, int nlib, edm_precision prec) {
 }
 
 edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, const uint8_t *tables,
-                         size_t slot_bytes, const int32_t *E_lib, int lib0, int nlib, int tau,
-                         int Tp, edm_precision prec, const double *ysum, const double *yysum,
-                         float *rho, long long rho_ld) {
+                         const CcmGroups &g, int lib0, int nlib, int tau, int Tp,
+                         edm_precision prec, const double *ysum, const double *yysum, float *rho,
+                         long long rho_ld) {
     const bool bf16 = prec == EDM_BF16_TARGETS;
     const int tt = targets_per_tile(prec);
     const int n_tiles = (N_tgt + tt - 1) / tt;
-    const int nm = bf16 ? 6 : 3;
-    const int LK_NC = bf16 ? LkWarps<true>::NC : LkWarps<false>::NC;
-    const int threads = bf16 ? LkWarps<true>::THREADS : LkWarps<false>::THREADS;
+    const int threads = bf16 ? LkCfg<true>::THREADS : LkCfg<false>::THREADS;
+    const int G = bf16 ? LkCfg<true>::G : LkCfg<false>::G;
+    if (g.G != G) return set_error(ctx, EDM_ERR_INTERNAL, "lookup: group size mismatch");
+    const size_t red_bytes =
+        sizeof(float) * (bf16 ? LkCfg<true>::RED_FLOATS : LkCfg<false>::RED_FLOATS);
     const size_t tile_bytes = static_cast<size_t>(L + 1) * LK_TILE_ROW;
-    const size_t fixed = static_cast<size_t>(2) * LK_NC * nm * 32 * sizeof(float) +
-                         (2 * LK_MAX_STAGES + 5) * sizeof(uint64_t);
+    const size_t fixed = red_bytes + (2 * LK_MAX_STAGES + 4) * sizeof(uint64_t);
     const size_t limit = static_cast<size_t>(ctx->max_smem_optin);
-    const bool smem_tile =
-        tile_bytes + fixed + 2 * LK_STAGE_BYTES <= limit && tile_bytes < (1u << 20);
+    // stages of 6 KB (4 KB when the tile leaves less room); at least two
+    const size_t min_stage = 4096, big_stage = 6144;
+    const bool smem_tile = tile_bytes + fixed + 2 * min_stage <= limit && tile_bytes < (1u << 20);
     const size_t avail = limit - fixed - (smem_tile ? tile_bytes : 0);
-    const int stages = static_cast<int>(std::min<size_t>(LK_MAX_STAGES, avail / LK_STAGE_BYTES));
+    const size_t stage_bytes = avail >= 2 * big_stage ? big_stage : min_stage;
+    const int stages = static_cast<int>(std::min<size_t>(LK_MAX_STAGES, avail / stage_bytes));
     if (stages < 2) return set_error(ctx, EDM_ERR_INTERNAL, "lookup: no room for table stages");
-    const size_t smem = (smem_tile ? tile_bytes : 0) + static_cast<size_t>(stages) * LK_STAGE_BYTES +
-                        static_cast<size_t>(2) * LK_NC * nm * 32 * sizeof(float) +
-                        (2 * stages + 5) * sizeof(uint64_t);
+    const size_t smem = (smem_tile ? tile_bytes : 0) + static_cast<size_t>(stages) * stage_bytes +
+                        red_bytes + (2 * stages + 4) * sizeof(uint64_t);
 
     // libraries per CTA: a fixed override, else the autotuned value of this
-    // launch's bucket, else the heuristic
+    // launch's bucket, else the heuristic; a CTA takes lb / G groups
     long long lb = lookup_default_lb(ctx, nlib, n_tiles);
     if (ctx->lookup_lb > 0) {
         lb = std::min(ctx->lookup_lb, nlib);
@@ -497,25 +539,25 @@ edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, cons
         auto it = ctx->tune->find(lookup_bucket(L, N_tgt, nlib, prec));
         if (it != ctx->tune->end()) lb = std::min(it->second, nlib);
     }
+    const int GB = static_cast<int>(std::max<long long>(1, lb / G));
     LookupArgs a;
     a.Yt = Yt;
     a.tables = tables;
-    a.slot_bytes = slot_bytes;
-    a.E_lib = E_lib;
+    a.grp = g;
     a.ysum = ysum;
     a.yysum = yysum;
     a.lib0 = lib0;
-    a.nlib = nlib;
-    a.LB = static_cast<int>(lb);
+    a.GB = GB;
     a.L = L;
     a.tau = tau;
     a.Tp = Tp;
     a.N_tgt = N_tgt;
     a.stages = stages;
+    a.stage_bytes = static_cast<int>(stage_bytes);
     a.rho = rho;
     a.rho_ld = rho_ld;
     a.flags = ctx->d_flags;
-    dim3 grid(n_tiles, static_cast<unsigned>((nlib + lb - 1) / lb));
+    dim3 grid(n_tiles, static_cast<unsigned>((g.ngroups_max + GB - 1) / GB));
     void (*kern)(const LookupArgs);
     if (bf16)
         kern = smem_tile ? lookup_kernel<true, true> : lookup_kernel<true, false>;

@@ -20,6 +20,30 @@ namespace edm {
 constexpr int SX_WARPS = 8;
 constexpr int SX_SERIES_SMEM_MAX = 96 * 1024;
 
+// Simplex prediction from the K neighbours held one per lane (lane r < K
+// holds the r-th nearest: time u, distance d): sum_r w_r y_r / sum_r w_r with
+// w_r = exp(-d_r/d_1) (or the d_1 = 0 limit) and y_r = x[u_r+Tp] - mu.  The
+// two sums are reduced side by side.
+__device__ __forceinline__ float simplex_predict(float d, int u, const float *xs, int Tp, float mu,
+                                                 int K) {
+    const int lane = lane_id();
+    const float d1 = __shfl_sync(FULL, d, 0);
+    float w = 0.f, wy = 0.f;
+    if (lane < K) {
+        if (d1 > 0.f)
+            w = expf(-(d / d1));
+        else
+            w = (d == 0.f) ? 1.f : 0.f;
+        wy = w * __fsub_rn(xs[u + Tp], mu);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        w += __shfl_xor_sync(FULL, w, o);
+        wy += __shfl_xor_sync(FULL, wy, o);
+    }
+    return wy / w;
+}
+
 template <int E>
 __device__ __forceinline__ void simplex_row(const float *xs, int t, int lo, int hi, int tau, int Tp,
                                             float mu, WarpScratch *ws, float (&m)[5]) {
@@ -28,9 +52,7 @@ __device__ __forceinline__ void simplex_row(const float *xs, int t, int lo, int 
     int u = 0;
     float d = 0.f;
     knn_row<E, KNN_SET>(xs, t, lo, hi, tau, K, ws, &u, &d);
-    const float w = simplex_weight(d, K);
-    const float part = lane < K ? w * __fsub_rn(xs[u + Tp], mu) : 0.f;
-    const float a = warp_sum(part);
+    const float a = simplex_predict(d, u, xs, Tp, mu, K);
     const float b = __fsub_rn(xs[t + Tp], mu);
     if (lane == E - 1) {
         m[0] += a;
@@ -149,9 +171,7 @@ __device__ __forceinline__ void sweep_row(const float *xs, int t, int hi, int E_
         int u_out = 0;
         float d_out = 0.f;
         select_set_regs<CH>(s, xs, t, lo, hi, E, tau, K, ws, u_out, d_out);
-        const float w = simplex_weight(d_out, K);
-        const float part = lane < K ? w * __fsub_rn(xs[u_out + Tp], mu) : 0.f;
-        const float a = warp_sum(part);
+        const float a = simplex_predict(d_out, u_out, xs, Tp, mu, K);
         const float b = __fsub_rn(xs[t + Tp], mu);
         if (lane == E - 1) {
             m[0] += a;
@@ -340,9 +360,7 @@ __device__ void sweep_long_row(const float *xs, int L, int t, int hi, int E_max,
             }
         }
         __syncwarp();
-        const float w = simplex_weight(d_out, K);
-        const float part = lane < K ? w * __fsub_rn(xs[u_out + Tp], mu) : 0.f;
-        const float a = warp_sum(part);
+        const float a = simplex_predict(d_out, u_out, xs, Tp, mu, K);
         const float b = __fsub_rn(xs[t + Tp], mu);
         if (lane == E - 1) {
             m[0] += a;
