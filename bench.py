@@ -333,13 +333,127 @@ def run_gb300(args):
         print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------ other workloads
+
+def sync_time(fn, dev, stream, steps):
+    """Mean milliseconds of fn() over `steps` calls, CUDA events on `stream`."""
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return e0.elapsed_time(e1) / steps
+
+
+def log(msg):
+    sys.stderr.write("[bench %.0fs] %s\n" % (time.perf_counter() - T_START, msg))
+    sys.stderr.flush()
+
+
+T_START = time.perf_counter()
+
+
+def run_batched_workload(args):
+    """256 independent all-to-all CCM problems of uneven N and L (optimal E,
+    then CCM), batched (graph-captured, concurrent streams) against the same
+    problems launched one after another on one stream.  Optimal E is timed
+    once per mode; the CCM step per mode and target precision."""
+    from paper_2105_12301_gb300 import edm
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    Ns, Ls = inputs.config4_shapes()
+    probs, E_out, pairs = [], [], 0.0
+    for i, (N, L) in enumerate(zip(Ns, Ls)):
+        X = torch.from_numpy(inputs.config4_instance(i, N, L)).to(dev)
+        E = torch.empty(int(N), dtype=torch.int32, device=dev)
+        rho = torch.empty((int(N), int(N)), dtype=torch.float32, device=dev)
+        probs.append({"X": X, "tau": TAU, "Tp": TP, "E_lib": E, "rho": rho})
+        E_out.append(E)
+        pairs += float(N) * float(N)
+    log("generated %d instances, %.3g pairs" % (len(probs), pairs))
+
+    def opt_E():
+        edm.edm_simplex_optimal_E_batched(probs, E_MAX, TP_SEL, out=E_out)
+
+    out = {"metric": METRIC, "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+           "config": {"workload": "256 independent coupled-logistic CCM problems, N log-uniform "
+                                  "in [32, 2048], L log-uniform in [200, 5000], noise 0.02",
+                      "pairs_per_step": pairs, "E_range": [1, E_MAX], "tau": TAU, "Tp": TP,
+                      "Tp_sel": TP_SEL}}
+    for mode, opts in (("batched", {"batch_graph": 1, "batch_streams": 8}),
+                       ("per_instance", {"batch_graph": 0, "batch_streams": 1})):
+        for k, v in opts.items():
+            edm.edm_set_option(k, v, dev)
+        opt_E()
+        ms_E = sync_time(opt_E, dev, stream, 1)
+        log("%s optimal E %.1f ms" % (mode, ms_E))
+        rec = {"optimal_E_ms": ms_E}
+        for prec in ("fp32", "bf16"):
+            def ccm():
+                edm.edm_ccm_batched(probs, prec)
+            for _ in range(max(1, args.warmup)):
+                ccm()
+            ms = sync_time(ccm, dev, stream, max(1, args.steps))
+            edm.edm_ctx_sync(dev)
+            log("%s ccm %s %.1f ms" % (mode, prec, ms))
+            rec[prec] = {"ccm_ms": ms, "value": pairs / ((ms + ms_E) / 1e3),
+                         "ms_per_step": ms + ms_E}
+        out[mode] = rec
+    out["value"] = out["batched"]["fp32"]["value"]
+    out["ms_per_step"] = out["batched"]["fp32"]["ms_per_step"]
+    print(json.dumps(out), flush=True)
+
+
+def run_libsweep_workload(args):
+    """Library-length convergence: 2,000 coupled-logistic series x 10,000
+    steps; E per library from the full-length simplex, then all-to-all CCM on
+    the window [0, L_lib) for L_lib = 100 .. 10,000."""
+    from paper_2105_12301_gb300 import edm
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    X = inputs.config5()
+    N, L = X.shape
+    Xg = torch.from_numpy(X).to(dev)
+    log("generated %d x %d" % (N, L))
+    ms_E = sync_time(lambda: edm.edm_simplex_optimal_E(Xg, E_MAX, TAU, TP_SEL, with_rho=False),
+                     dev, stream, 1)
+    log("optimal E %.1f ms" % ms_E)
+    E_full, _ = edm.edm_simplex_optimal_E(Xg, E_MAX, TAU, TP_SEL, with_rho=False)
+    rho = torch.empty((N, N), dtype=torch.float32, device=dev)
+    sizes = {}
+    for L_lib in (100, 300, 1000, 3000, 10000):
+        for prec in ("fp32", "bf16"):
+            def one():
+                edm.edm_ccm_window(Xg, 0, L_lib, E_full, TAU, TP, prec, out=rho)
+            one()
+            ms = sync_time(one, dev, stream, max(1, args.steps))
+            edm.edm_ctx_sync(dev)
+            sizes.setdefault(str(L_lib), {})[prec] = {"value": N * N / (ms / 1e3),
+                                                      "ms": ms}
+            log("window %d %s %.1f ms" % (L_lib, prec, ms))
+    out = {"metric": METRIC, "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
+           "data": "synthetic", "value": sizes["10000"]["fp32"]["value"],
+           "config": {"workload": "library-length sweep, %d coupled-logistic series x %d steps, "
+                                  "windows [0, L_lib)" % (N, L), "pairs_per_size": N * N},
+           "optimal_E_ms": ms_E, "per_library_size": sizes,
+           "E_opt_hist": np.bincount(E_full.cpu().numpy(), minlength=E_MAX + 1)[1:].tolist()}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["calcium50k", "calcium2k"], default="calcium50k")
+    ap.add_argument("--workload", choices=["calcium50k", "calcium2k", "batched", "libsweep"],
+                    default="calcium50k")
     ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
@@ -347,6 +461,10 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched_workload(args)
+    elif args.workload == "libsweep":
+        run_libsweep_workload(args)
     else:
         run_gb300(args)
 

@@ -110,6 +110,15 @@ edm_status edm_profile_read(edm_ctx *ctx, const char *kernel, double *total_ms,
  * pattern, one conflict-free wavefront per read) for about `ms` ms. */
 edm_status edm_probe_smem_bandwidth(edm_ctx *ctx, double ms, double *bytes_per_s);
 
+/* Failure-detection check (no counterpart in the paper).  Every wait inside
+ * a libedm kernel is bounded: after its limit it records EDM_ERR_TIMEOUT in
+ * the context and the kernel runs to its end, so a lost arrival never hangs
+ * the GPU.  This call enqueues one thread that waits, with that same bounded
+ * wait, on a barrier nothing completes, giving up after `ms` milliseconds
+ * (1..10000).  The next edm_ctx_sync then returns EDM_ERR_TIMEOUT (and
+ * clears it); the context stays usable. */
+edm_status edm_check_wait_timeout(edm_ctx *ctx, int ms);
+
 /* Section 2.1 step 1: time-delay embedding of one series.
  * x [L] float32; out [L-(E-1)tau][E] float32, row i = time (E-1)tau+i,
  * column l = x[t - l*tau].  1 <= E <= EDM_E_MAX, tau >= 1, (E-1)tau < L. */
@@ -178,6 +187,21 @@ edm_status edm_ccm_all(edm_ctx *ctx, const float *X_lib, int N_lib,
                        const float *Y_tgt, int N_tgt, int L,
                        const int32_t *E_lib, int tau, int Tp,
                        edm_precision prec, float *rho);
+
+/* Section 2.1 step 3 / Algorithm 3 with its output written: simplex
+ * predictions (forecasts at horizon Tp) of target series from library
+ * manifolds.  X_lib [N_lib][L], Y_tgt [N_tgt][L] float32; E_lib [N_lib] int32
+ * (device); tgt_of_lib [N_lib] int32 (device): the target row each library
+ * predicts, or NULL for target i = library i (then N_tgt >= N_lib).
+ * pred [N_lib][L] float32: pred[i][t+Tp] = sum_r w_r Y_j[u_r+Tp] for every
+ * library point t of library i (j its target, u_r its neighbours, w_r the
+ * normalised simplex weights); every other entry is NaN.  With Y = X and
+ * tgt_of_lib = NULL this is the leave-one-out simplex forecast of each
+ * series.  An E or a target index out of range gives a NaN row and
+ * EDM_ERR_INVALID_ARG from the next edm_ctx_sync. */
+edm_status edm_predict(edm_ctx *ctx, const float *X_lib, int N_lib, const float *Y_tgt,
+                       int N_tgt, int L, const int32_t *E_lib, const int32_t *tgt_of_lib,
+                       int tau, int Tp, float *pred);
 
 /* Convergence with library length (the "convergent" of CCM, section 2.1):
  * all-to-all CCM restricted to the window X[i][offset .. offset+L_win) of

@@ -486,6 +486,14 @@ edm_status edm_probe_smem_bandwidth(edm_ctx *ctx, double ms, double *bytes_per_s
 
 uint64_t edm_kernel_launches(edm_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
+edm_status edm_check_wait_timeout(edm_ctx *ctx, int ms) {
+    if (!ctx) return EDM_ERR_INVALID_ARG;
+    if (ms < 1 || ms > 10000)
+        return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_check_wait_timeout: ms out of range");
+    DeviceGuard g(ctx->device);
+    return launch_wait_check(ctx, ms);
+}
+
 edm_status edm_embed(edm_ctx *ctx, const float *x, int L, int E, int tau, float *out) {
     if (!ctx) return EDM_ERR_INVALID_ARG;
     if (!x || !out || !series_len_ok(L) || E < 1 || E > EDM_E_MAX || tau < 1 ||
@@ -540,6 +548,37 @@ edm_status edm_ccm_window(edm_ctx *ctx, const float *X, int N, int ld, int offse
     DeviceGuard g(ctx->device);
     const float *base = X + offset;
     return ccm_one(ctx, base, ld, N, base, ld, N, L_win, E_lib, tau, Tp, prec, rho);
+}
+
+edm_status edm_predict(edm_ctx *ctx, const float *X_lib, int N_lib, const float *Y_tgt, int N_tgt,
+                       int L, const int32_t *E_lib, const int32_t *tgt_of_lib, int tau, int Tp,
+                       float *pred) {
+    if (!ctx) return EDM_ERR_INVALID_ARG;
+    if (!X_lib || !Y_tgt || !E_lib || !pred || N_lib < 1 || N_tgt < 1 || !series_len_ok(L) ||
+        tau < 1 || Tp < 0 || L - Tp < 3 || (!tgt_of_lib && N_tgt < N_lib))
+        return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_predict: bad arguments");
+    DeviceGuard g(ctx->device);
+    const size_t slot = ccm_slot_bytes(L, tau, Tp);
+    if (slot == 0) return set_error(ctx, EDM_ERR_INVALID_ARG, "series too short");
+    const int G = LK_GROUP_FP32;
+    const int chunk = ccm_chunk(ctx, N_lib, slot, G);
+    edm_status st = ws_reserve(ctx, groups_bytes(chunk, G) +
+                                        static_cast<size_t>(groups_max(chunk, G)) * G * slot);
+    if (st != EDM_OK) return st;
+    uint8_t *gmem = static_cast<uint8_t *>(ctx->ws);
+    uint8_t *tables = gmem + groups_bytes(chunk, G);
+    for (int c0 = 0; c0 < N_lib; c0 += chunk) {
+        const int nlib = std::min(chunk, N_lib - c0);
+        const CcmGroups grp = carve_groups(gmem, nlib, G);
+        st = launch_group_libs(ctx, E_lib, c0, nlib, L, tau, Tp, grp);
+        if (st != EDM_OK) return st;
+        st = launch_ccm_tables(ctx, X_lib, L, nlib, L, tau, Tp, grp, tables);
+        if (st != EDM_OK) return st;
+        st = launch_predict(ctx, Y_tgt, L, N_tgt, tgt_of_lib, L, tau, Tp, grp, tables, c0,
+                            pred + static_cast<size_t>(c0) * L, L);
+        if (st != EDM_OK) return st;
+    }
+    return EDM_OK;
 }
 
 static bool instance_ok(const edm_instance &p) {

@@ -149,7 +149,13 @@ edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L,
                          const uint8_t *tables, const CcmGroups &g, int lib0, int nlib, int tau,
                          int Tp, edm_precision prec, const double *ysum, const double *yysum,
                          float *rho, long long rho_ld);
+// Predictions of libraries lib0.. (groups g, tables built by launch_ccm_tables)
+// for their targets Y[tgt_of[lib]] (Y[lib] when tgt_of is NULL).
+edm_status launch_predict(edm_ctx *ctx, const float *Y, long long ld_tgt, int N_tgt,
+                          const int32_t *tgt_of, int L, int tau, int Tp, const CcmGroups &g,
+                          const uint8_t *tables, int lib0, float *pred, long long ld_pred);
 edm_status launch_smem_probe(edm_ctx *ctx, double ms, double *bytes_per_s);
+edm_status launch_wait_check(edm_ctx *ctx, int ms);
 size_t simplex_workspace_bytes(edm_ctx *ctx, int N, int L, int E_max);
 // Autotuner bucket of a lookup launch.
 uint64_t lookup_bucket(int L, int N_tgt, int nlib, edm_precision prec);
@@ -255,16 +261,18 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
     return t;
 }
 
-// Wait for the phase with the given parity to complete, for at most about
-// two seconds.  On timeout the context's error flag is raised and false is
-// returned; the caller carries on (its data is then garbage) so that every
-// thread still reaches every later barrier and the kernel always ends.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *flags) {
+// Wait for the phase with the given parity to complete, for at most
+// limit_ns nanoseconds (two seconds by default).  On timeout the context's
+// error flag is raised and false is returned; the caller carries on (its
+// data is then garbage) so that every thread still reaches every later
+// barrier and the kernel always ends.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *flags,
+                                                  uint64_t limit_ns = 2000000000ull) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (global_timer_ns() - t0 > 2000000000ull) {
+        if (global_timer_ns() - t0 > limit_ns) {
             set_flag(flags, EDMF_TIMEOUT);
             return false;
         }

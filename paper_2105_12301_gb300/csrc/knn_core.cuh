@@ -30,7 +30,7 @@ namespace edm {
 constexpr int KNN_CAP = 128;     // per-warp candidate buffer
 constexpr int KNN_MARGIN = 8;    // extra FP32 candidates re-ranked in FP64
 
-struct WarpScratch {
+struct alignas(16) WarpScratch {
     uint64_t key[KNN_CAP];   // collected FP32 keys
     double s64[KNN_CAP];     // their FP64 squared distances (band fallback)
     uint64_t sel[32];        // the R smallest collected keys, ascending
@@ -114,13 +114,22 @@ __device__ __forceinline__ int filter_keys(const float (&q)[E], const float *xs,
 }
 
 // Rank the c (<= KNN_CAP) keys of ws->key; write the R smallest, ascending,
-// to ws->sel.
+// to ws->sel.  The buffer is padded to a multiple of four with keys above
+// every real key (a real key's high word is a finite float), and read two
+// keys per 16-byte load.
 __device__ __forceinline__ void rank_keys(WarpScratch *ws, int c, int R) {
     const int lane = lane_id();
+    const int c4 = (c + 3) & ~3;  // <= KNN_CAP, a multiple of four
+    if (lane < c4 - c) ws->key[c + lane] = ~0ull;
+    __syncwarp();
+    const ulonglong2 *k2 = reinterpret_cast<const ulonglong2 *>(ws->key);
     for (int e = lane; e < c; e += WARP) {
-        uint64_t ke = ws->key[e];
+        const uint64_t ke = ws->key[e];
         int rank = 0;
-        for (int e2 = 0; e2 < c; ++e2) rank += ws->key[e2] < ke;
+        for (int e2 = 0; e2 < c4 / 2; e2 += 2) {
+            const ulonglong2 a = k2[e2], b = k2[e2 + 1];
+            rank += (a.x < ke) + (a.y < ke) + (b.x < ke) + (b.y < ke);
+        }
         if (rank < R) ws->sel[rank] = ke;
     }
     __syncwarp();

@@ -72,4 +72,21 @@ edm_status launch_smem_probe(edm_ctx *ctx, double ms, double *bytes_per_s) {
     return st;
 }
 
+// One thread waits, with the bounded wait every pipelined kernel of the
+// library uses, on an mbarrier that expects one arrival which never comes.
+// The wait gives up after `ms` milliseconds and raises the timeout flag.
+__global__ void wait_check_kernel(uint64_t limit_ns, int *flags) {
+    __shared__ uint64_t bar;
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+    mbar_wait_bounded(&bar, 0, flags, limit_ns);
+}
+
+edm_status launch_wait_check(edm_ctx *ctx, int ms) {
+    before_launch(ctx);
+    wait_check_kernel<<<1, 1, 0, ctx->stream>>>(static_cast<uint64_t>(ms) * 1000000ull,
+                                                ctx->d_flags);
+    return after_launch(ctx, "wait_check_kernel");
+}
+
 }  // namespace edm

@@ -76,6 +76,8 @@ def load():
                                                   ctypes.POINTER(vp)]
     lib.edm_set_option.argtypes = [vp, ctypes.c_char_p, ctypes.c_longlong]
     lib.edm_simplex_optimal_E_noalloc.argtypes = [vp, ci, ci, ci, ci, ci, vp, vp, vp]
+    lib.edm_check_wait_timeout.argtypes = [vp, ci]
+    lib.edm_predict.argtypes = [vp, vp, ci, vp, ci, ci, vp, vp, ci, ci, vp]
     lib.edm_profile_enable.argtypes = [vp, ci]
     lib.edm_profile_read.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ci)]
@@ -85,7 +87,8 @@ def load():
               "edm_knn", "edm_simplex_optimal_E", "edm_ccm_all", "edm_ccm_batched",
               "edm_profile_enable", "edm_profile_read", "edm_probe_smem_bandwidth",
               "edm_simplex_optimal_E_noalloc", "edm_ccm_window",
-              "edm_simplex_optimal_E_batched", "edm_set_option"):
+              "edm_simplex_optimal_E_batched", "edm_set_option", "edm_check_wait_timeout",
+              "edm_predict"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -166,6 +169,14 @@ def edm_probe_smem_bandwidth(ms=200.0, device=None):
     _check(ctx, load().edm_probe_smem_bandwidth(ctx, float(ms), ctypes.byref(bw)),
            "edm_probe_smem_bandwidth")
     return bw.value
+
+
+def edm_check_wait_timeout(ms=50, device=None):
+    """Enqueue a bounded device-side wait that nothing completes; the next
+    edm_ctx_sync raises EdmError(EDM_ERR_TIMEOUT)."""
+    dev = device if device is not None else torch.cuda.current_device()
+    ctx = _ctx(dev)
+    _check(ctx, load().edm_check_wait_timeout(ctx, int(ms)), "edm_check_wait_timeout")
 
 
 def edm_embed(x, E, tau=1):
@@ -255,6 +266,30 @@ def edm_ccm_all(X_lib, Y_tgt, E_lib, tau=1, Tp=0, precision="fp32", out=None):
     return rho
 
 
+def edm_predict(X_lib, Y_tgt, E_lib, tgt_of_lib=None, tau=1, Tp=0, out=None):
+    """pred [N_lib][L]: simplex prediction of target tgt_of_lib[i] (target i
+    when None) from library i's manifold at time t+Tp for every library point
+    t; NaN elsewhere."""
+    _series(X_lib, "X_lib", 2)
+    _series(Y_tgt, "Y_tgt", 2)
+    if X_lib.shape[1] != Y_tgt.shape[1]:
+        raise ValueError("libraries and targets must have the same length")
+    N_lib, L = X_lib.shape
+    for name, a in (("E_lib", E_lib), ("tgt_of_lib", tgt_of_lib)):
+        if a is not None and (a.dtype != torch.int32 or not a.is_cuda or a.shape != (N_lib,)):
+            raise TypeError("%s must be a CUDA int32 tensor of shape [N_lib]" % name)
+    pred = out if out is not None else torch.empty((N_lib, L), dtype=torch.float32,
+                                                   device=X_lib.device)
+    if pred.shape != (N_lib, L) or pred.dtype != torch.float32 or not pred.is_contiguous():
+        raise TypeError("out must be a contiguous float32 [N_lib][L] tensor")
+    tgt = tgt_of_lib.contiguous() if tgt_of_lib is not None else None
+    ctx = _ctx(X_lib.device)
+    _check(ctx, load().edm_predict(ctx, _ptr(X_lib), N_lib, _ptr(Y_tgt), Y_tgt.shape[0], L,
+                                   _ptr(E_lib.contiguous()), _ptr(tgt), tau, Tp, _ptr(pred)),
+           "edm_predict")
+    return pred
+
+
 def edm_ccm_window(X, offset, L_win, E_lib, tau=1, Tp=0, precision="fp32", out=None):
     """rho [N][N] of all-to-all CCM on the windows X[:, offset:offset+L_win]."""
     _series(X, "X", 2)
@@ -294,13 +329,21 @@ def _instances(problems):
     return arr, keep
 
 
-def edm_simplex_optimal_E_batched(problems, E_max=EDM_E_MAX, Tp_sel=1):
-    """Optimal E of every series of every problem (dicts with X, tau)."""
+def edm_simplex_optimal_E_batched(problems, E_max=EDM_E_MAX, Tp_sel=1, out=None):
+    """Optimal E of every series of every problem (dicts with X, tau).  `out`:
+    optional list of CUDA int32 [N_i] tensors to write (the same tensors on
+    every call let a captured batch be replayed)."""
     if not problems:
         return []
     arr, keep = _instances(problems)
-    outs = [torch.empty(p["X"].shape[0], dtype=torch.int32, device=p["X"].device)
-            for p in problems]
+    if out is None:
+        outs = [torch.empty(p["X"].shape[0], dtype=torch.int32, device=p["X"].device)
+                for p in problems]
+    else:
+        outs = list(out)
+        for o, p in zip(outs, problems):
+            if o.dtype != torch.int32 or o.shape != (p["X"].shape[0],) or not o.is_cuda:
+                raise TypeError("out[i] must be a CUDA int32 tensor of shape [N_i]")
     ptrs = (ctypes.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
     ctx = _ctx(problems[0]["X"].device)
     _check(ctx, load().edm_simplex_optimal_E_batched(ctx, arr, len(problems), E_max, Tp_sel, ptrs),

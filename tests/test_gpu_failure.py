@@ -1,0 +1,34 @@
+"""Failure detection without a GPU fault: every wait inside a libedm kernel is
+bounded, records EDM_ERR_TIMEOUT in the context when it gives up, and lets
+the kernel run to its end, so the context stays usable."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2105_12301_gb300 import edm, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable():
+    edm.edm_ctx_sync()                      # start from a clean flag
+    edm.edm_check_wait_timeout(50)          # a wait nothing completes, 50 ms limit
+    with pytest.raises(edm.EdmError) as err:
+        edm.edm_ctx_sync()
+    assert err.value.status == 4            # EDM_ERR_TIMEOUT
+    edm.edm_ctx_sync()                      # the flag was cleared by the read
+    X = inputs.config1()[:6]
+    Xg = torch.from_numpy(X).cuda()
+    E = np.array([2, 3, 1, 2, 4, 2], np.int32)
+    rho = edm.edm_ccm_all(Xg, Xg, torch.from_numpy(E).cuda(), 1, 0, "fp32")
+    edm.edm_ctx_sync()
+    ref = oracle.ccm_matrix(X, X, E, 1, 0)
+    assert np.max(np.abs(rho.cpu().numpy() - ref)) <= 1e-5
+
+
+def test_wait_check_rejects_bad_limits():
+    with pytest.raises(edm.EdmError):
+        edm.edm_check_wait_timeout(0)
+    with pytest.raises(edm.EdmError):
+        edm.edm_check_wait_timeout(20000)
