@@ -188,6 +188,20 @@ edm_status edm_ccm_all(edm_ctx *ctx, const float *X_lib, int N_lib,
                        const int32_t *E_lib, int tau, int Tp,
                        edm_precision prec, float *rho);
 
+/* Pairwise CCM with the embedding dimension chosen per TARGET (section 3.3:
+ * targets are grouped by their optimal E, and for each group every library
+ * is embedded at that E and gets one neighbour table).  Arguments as for
+ * edm_ccm_all, except E_tgt [N_tgt] int32 (device): the E of each target;
+ * rho[i][j] is then the skill of library i embedded at E_tgt[j] predicting
+ * target j.  The call reads E_tgt back to the host (it synchronises the
+ * context's stream once) and runs one CCM pass per distinct E.  An E_tgt
+ * value outside 1..EDM_E_MAX, or one leaving fewer than E+2 points, returns
+ * EDM_ERR_INVALID_ARG before any work is enqueued. */
+edm_status edm_ccm_all_target_E(edm_ctx *ctx, const float *X_lib, int N_lib,
+                                const float *Y_tgt, int N_tgt, int L,
+                                const int32_t *E_tgt, int tau, int Tp,
+                                edm_precision prec, float *rho);
+
 /* Section 2.1 step 3 / Algorithm 3 with its output written: simplex
  * predictions (forecasts at horizon Tp) of target series from library
  * manifolds.  X_lib [N_lib][L], Y_tgt [N_tgt][L] float32; E_lib [N_lib] int32

@@ -122,9 +122,15 @@ static size_t ccm_workspace_bytes(edm_ctx *ctx, int N_lib, int N_tgt, int L, int
            static_cast<size_t>(groups_max(chunk, G)) * G * slot;
 }
 
+// E_lib: E per library, unless E_uniform > 0 (every library at that E).
+// The N_tgt stored targets are Y rows tgt_rows[r] (rows 0.. when NULL); rho
+// rows are rho_ld apart and stored target r goes to column rho_cols[r]
+// (column r when NULL).
 static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, int N_lib,
                           const float *Y_tgt, long long ld_tgt, int N_tgt, int L,
-                          const int32_t *E_lib, int tau, int Tp, edm_precision prec, float *rho) {
+                          const int32_t *E_lib, int E_uniform, int tau, int Tp, edm_precision prec,
+                          float *rho, long long rho_ld, const int32_t *tgt_rows,
+                          const int32_t *rho_cols) {
     const size_t yt_bytes = target_store_bytes(N_tgt, L, prec);
     const size_t mean_bytes = align_up(sizeof(double) * N_tgt, 256);
     const size_t sums_bytes = align_up(sizeof(double) * N_tgt * EDM_E_MAX, 256);
@@ -141,17 +147,18 @@ static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, in
     double *yysum = reinterpret_cast<double *>(base + yt_bytes + mean_bytes + sums_bytes);
     uint8_t *gmem = base + yt_bytes + mean_bytes + 2 * sums_bytes;
     uint8_t *tables = gmem + groups_bytes(chunk, G);
-    st = launch_target_store(ctx, Y_tgt, ld_tgt, N_tgt, L, tau, Tp, prec, Yt, mean, ysum, yysum);
+    st = launch_target_store(ctx, Y_tgt, ld_tgt, tgt_rows, N_tgt, L, tau, Tp, prec, Yt, mean,
+                             ysum, yysum);
     if (st != EDM_OK) return st;
     for (int c0 = 0; c0 < N_lib; c0 += chunk) {
         const int nlib = std::min(chunk, N_lib - c0);
         const CcmGroups grp = carve_groups(gmem, nlib, G);
-        st = launch_group_libs(ctx, E_lib, c0, nlib, L, tau, Tp, grp);
+        st = launch_group_libs(ctx, E_lib, E_uniform, c0, nlib, L, tau, Tp, grp);
         if (st != EDM_OK) return st;
         st = launch_ccm_tables(ctx, X_lib, ld_lib, nlib, L, tau, Tp, grp, tables);
         if (st != EDM_OK) return st;
         st = launch_lookup(ctx, Yt, N_tgt, L, tables, grp, c0, nlib, tau, Tp, prec, ysum, yysum,
-                           rho + static_cast<size_t>(c0) * N_tgt, N_tgt);
+                           rho + static_cast<size_t>(c0) * rho_ld, rho_ld, rho_cols);
         if (st != EDM_OK) return st;
     }
     return EDM_OK;
@@ -535,7 +542,59 @@ edm_status edm_ccm_all(edm_ctx *ctx, const float *X_lib, int N_lib, const float 
         tau < 1 || Tp < 0 || L - Tp < 3 || (prec != EDM_FP32 && prec != EDM_BF16_TARGETS))
         return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_all: bad arguments");
     DeviceGuard g(ctx->device);
-    return ccm_one(ctx, X_lib, L, N_lib, Y_tgt, L, N_tgt, L, E_lib, tau, Tp, prec, rho);
+    return ccm_one(ctx, X_lib, L, N_lib, Y_tgt, L, N_tgt, L, E_lib, 0, tau, Tp, prec, rho, N_tgt,
+                   nullptr, nullptr);
+}
+
+edm_status edm_ccm_all_target_E(edm_ctx *ctx, const float *X_lib, int N_lib, const float *Y_tgt,
+                                int N_tgt, int L, const int32_t *E_tgt, int tau, int Tp,
+                                edm_precision prec, float *rho) {
+    if (!ctx) return EDM_ERR_INVALID_ARG;
+    if (!X_lib || !Y_tgt || !E_tgt || !rho || N_lib < 1 || N_tgt < 1 || !series_len_ok(L) ||
+        tau < 1 || Tp < 0 || L - Tp < 3 || (prec != EDM_FP32 && prec != EDM_BF16_TARGETS))
+        return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_all_target_E: bad arguments");
+    DeviceGuard g(ctx->device);
+    // the targets' E values decide which tables exist: read them (one sync)
+    std::vector<int32_t> E(N_tgt);
+    edm_status st = cuda_check(ctx, cudaMemcpyAsync(E.data(), E_tgt, sizeof(int32_t) * N_tgt,
+                                                    cudaMemcpyDeviceToHost, ctx->stream),
+                               "E_tgt read");
+    if (st == EDM_OK) st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "E_tgt read");
+    if (st != EDM_OK) return st;
+    std::vector<int32_t> order;  // target indexes grouped by E, ascending E
+    std::vector<int> begin(EDM_E_MAX + 2, 0);
+    for (int e = 1; e <= EDM_E_MAX; ++e) {
+        begin[e] = static_cast<int>(order.size());
+        for (int j = 0; j < N_tgt; ++j)
+            if (E[j] == e) order.push_back(j);
+    }
+    begin[EDM_E_MAX + 1] = static_cast<int>(order.size());
+    if (static_cast<int>(order.size()) != N_tgt)
+        return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_all_target_E: E_tgt out of 1..%d",
+                         EDM_E_MAX);
+    for (int e = 1; e <= EDM_E_MAX; ++e)
+        if (begin[e + 1] > begin[e] && !ccm_E_valid(e, L, tau, Tp))
+            return set_error(ctx, EDM_ERR_INVALID_ARG,
+                             "edm_ccm_all_target_E: E=%d leaves too few points", e);
+    // workspace: the largest CCM pass, then the target index list after it
+    const size_t ccm_bytes = align_up(ccm_workspace_bytes(ctx, N_lib, N_tgt, L, tau, Tp, prec), 256);
+    st = ws_reserve(ctx, ccm_bytes + sizeof(int32_t) * N_tgt);
+    if (st != EDM_OK) return st;
+    int32_t *d_order = reinterpret_cast<int32_t *>(static_cast<uint8_t *>(ctx->ws) + ccm_bytes);
+    st = cuda_check(ctx, cudaMemcpyAsync(d_order, order.data(), sizeof(int32_t) * N_tgt,
+                                         cudaMemcpyHostToDevice, ctx->stream), "target order");
+    // the host vector must outlive the copy
+    if (st == EDM_OK) st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "target order");
+    if (st != EDM_OK) return st;
+    for (int e = 1; e <= EDM_E_MAX; ++e) {
+        const int n = begin[e + 1] - begin[e];
+        if (n == 0) continue;
+        const int32_t *rows = d_order + begin[e];
+        st = ccm_one(ctx, X_lib, L, N_lib, Y_tgt, L, n, L, nullptr, e, tau, Tp, prec, rho, N_tgt,
+                     rows, rows);
+        if (st != EDM_OK) return st;
+    }
+    return EDM_OK;
 }
 
 edm_status edm_ccm_window(edm_ctx *ctx, const float *X, int N, int ld, int offset, int L_win,
@@ -547,7 +606,8 @@ edm_status edm_ccm_window(edm_ctx *ctx, const float *X, int N, int ld, int offse
         return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_window: bad arguments");
     DeviceGuard g(ctx->device);
     const float *base = X + offset;
-    return ccm_one(ctx, base, ld, N, base, ld, N, L_win, E_lib, tau, Tp, prec, rho);
+    return ccm_one(ctx, base, ld, N, base, ld, N, L_win, E_lib, 0, tau, Tp, prec, rho, N,
+                   nullptr, nullptr);
 }
 
 edm_status edm_predict(edm_ctx *ctx, const float *X_lib, int N_lib, const float *Y_tgt, int N_tgt,
@@ -570,7 +630,7 @@ edm_status edm_predict(edm_ctx *ctx, const float *X_lib, int N_lib, const float 
     for (int c0 = 0; c0 < N_lib; c0 += chunk) {
         const int nlib = std::min(chunk, N_lib - c0);
         const CcmGroups grp = carve_groups(gmem, nlib, G);
-        st = launch_group_libs(ctx, E_lib, c0, nlib, L, tau, Tp, grp);
+        st = launch_group_libs(ctx, E_lib, 0, c0, nlib, L, tau, Tp, grp);
         if (st != EDM_OK) return st;
         st = launch_ccm_tables(ctx, X_lib, L, nlib, L, tau, Tp, grp, tables);
         if (st != EDM_OK) return st;
@@ -618,8 +678,8 @@ edm_status edm_ccm_batched(edm_ctx *ctx, const edm_instance *inst, int n_inst,
     auto fn = [&](edm_ctx *sub, int j) {
         const edm_instance &p = inst[live[j]];
         return ccm_one(sub, p.X + static_cast<size_t>(p.lib_begin) * p.L, p.L,
-                       p.lib_end - p.lib_begin, p.X, p.L, p.N, p.L, p.E_lib + p.lib_begin, p.tau,
-                       p.Tp, prec, p.rho);
+                       p.lib_end - p.lib_begin, p.X, p.L, p.N, p.L, p.E_lib + p.lib_begin, 0,
+                       p.tau, p.Tp, prec, p.rho, p.N, nullptr, nullptr);
     };
     edm_status st = ensure_batch_state(ctx, std::max(1, std::min({ctx->batch_streams, n, 32})));
     if (st != EDM_OK) return st;

@@ -122,9 +122,10 @@ size_t groups_bytes(int nlib, int G);
 // Lay the group arrays out in `mem` (groups_bytes(nlib, G) bytes).
 CcmGroups carve_groups(uint8_t *mem, int nlib, int G);
 // Group the libraries lib0 .. lib0+nlib-1 by E (one CTA; order within an E
-// is not specified and does not change any result).
-edm_status launch_group_libs(edm_ctx *ctx, const int32_t *E_lib, int lib0, int nlib, int L,
-                             int tau, int Tp, const CcmGroups &g);
+// is not specified and does not change any result).  E of library i is
+// E_lib[i], or E_uniform for every library when E_uniform > 0.
+edm_status launch_group_libs(edm_ctx *ctx, const int32_t *E_lib, int E_uniform, int lib0,
+                             int nlib, int L, int tau, int Tp, const CcmGroups &g);
 
 // Launchers (one translation unit each).
 edm_status launch_embed(edm_ctx *ctx, const float *x, int L, int E, int tau, float *out);
@@ -140,15 +141,17 @@ edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max,
 // Transposed, centred target tiles plus, per E = 1..EDM_E_MAX, the FP64 sums
 // of the stored values and of their squares over the observation window of
 // E (times (E-1)tau+Tp .. L-1): ysum / yysum [EDM_E_MAX][N_tgt].
-// Y: target series with row stride ld (>= L) floats.
-edm_status launch_target_store(edm_ctx *ctx, const float *Y, long long ld, int N_tgt, int L,
-                               int tau, int Tp, edm_precision prec, uint8_t *Yt, double *mean_ws,
-                               double *ysum, double *yysum);
-// rho points at the row of library lib0; row of library i = rho + (i - lib0) * rho_ld.
+// Y: target series with row stride ld (>= L) floats; target r of the store is
+// series rows[r] (series r when rows is NULL).
+edm_status launch_target_store(edm_ctx *ctx, const float *Y, long long ld, const int32_t *rows,
+                               int N_tgt, int L, int tau, int Tp, edm_precision prec, uint8_t *Yt,
+                               double *mean_ws, double *ysum, double *yysum);
+// rho points at the row of library lib0; row of library i = rho + (i - lib0) * rho_ld;
+// stored target r goes to column rho_col[r] (column r when rho_col is NULL).
 edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L,
                          const uint8_t *tables, const CcmGroups &g, int lib0, int nlib, int tau,
                          int Tp, edm_precision prec, const double *ysum, const double *yysum,
-                         float *rho, long long rho_ld);
+                         float *rho, long long rho_ld, const int32_t *rho_col);
 // Predictions of libraries lib0.. (groups g, tables built by launch_ccm_tables)
 // for their targets Y[tgt_of[lib]] (Y[lib] when tgt_of is NULL).
 edm_status launch_predict(edm_ctx *ctx, const float *Y, long long ld_tgt, int N_tgt,

@@ -353,8 +353,8 @@ constexpr int GROUP_THREADS = 1024;
 // bucket in bucket order with the byte offsets of their tables, then every
 // library placed in a slot of its bucket's groups.
 __global__ void __launch_bounds__(GROUP_THREADS)
-    group_libs_kernel(const int32_t *__restrict__ E_lib, int lib0, int nlib, int L, int tau,
-                      int Tp, const CcmGroups g) {
+    group_libs_kernel(const int32_t *__restrict__ E_lib, int E_uniform, int lib0, int nlib, int L,
+                      int tau, int Tp, const CcmGroups g) {
     __shared__ int cnt[EDM_E_MAX + 1], fill[EDM_E_MAX + 1], gbase[EDM_E_MAX + 2];
     __shared__ long long obase[EDM_E_MAX + 1], gbytes[EDM_E_MAX + 1];
     const int tid = threadIdx.x, G = g.G;
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(GROUP_THREADS)
     for (int s = tid; s < g.ngroups_max * G; s += GROUP_THREADS) g.lib[s] = -1;
     __syncthreads();
     for (int i = tid; i < nlib; i += GROUP_THREADS) {
-        const int E = E_lib[lib0 + i];
+        const int E = E_uniform > 0 ? E_uniform : E_lib[lib0 + i];
         atomicAdd(&cnt[ccm_E_valid(E, L, tau, Tp) ? E : 0], 1);
     }
     __syncthreads();
@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(GROUP_THREADS)
         g.off[gi] = obase[b] + j * gbytes[b];
     }
     for (int i = tid; i < nlib; i += GROUP_THREADS) {
-        const int E = E_lib[lib0 + i];
+        const int E = E_uniform > 0 ? E_uniform : E_lib[lib0 + i];
         const int b = ccm_E_valid(E, L, tau, Tp) ? E : 0;
         const int pos = atomicAdd(&fill[b], 1);
         g.lib[(gbase[b] + pos / G) * G + pos % G] = lib0 + i;
@@ -412,10 +412,11 @@ __global__ void __launch_bounds__(GROUP_THREADS)
     }
 }
 
-edm_status launch_group_libs(edm_ctx *ctx, const int32_t *E_lib, int lib0, int nlib, int L,
-                             int tau, int Tp, const CcmGroups &g) {
+edm_status launch_group_libs(edm_ctx *ctx, const int32_t *E_lib, int E_uniform, int lib0,
+                             int nlib, int L, int tau, int Tp, const CcmGroups &g) {
     before_launch(ctx);
-    group_libs_kernel<<<1, GROUP_THREADS, 0, ctx->stream>>>(E_lib, lib0, nlib, L, tau, Tp, g);
+    group_libs_kernel<<<1, GROUP_THREADS, 0, ctx->stream>>>(E_lib, E_uniform, lib0, nlib, L, tau,
+                                                            Tp, g);
     return after_launch(ctx, "group_libs_kernel");
 }
 

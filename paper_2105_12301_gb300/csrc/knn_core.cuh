@@ -350,6 +350,44 @@ __device__ __forceinline__ int compact_le(const float (&s)[CH], float bound, War
 }
 
 
+// Warp-wide number of register slots with s <= b.
+template <int CH>
+__device__ __forceinline__ int warp_count_le(const float (&s)[CH], float b) {
+    int c = 0;
+#pragma unroll
+    for (int j = 0; j < CH; ++j) c += s[j] <= b ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+    return c;
+}
+
+// Shrink a bound that too many values lie under.  On entry `hi` is a bound
+// with c_hi > cap values of s at or below it, and at least `need` values of
+// s plus extra(b) lie at or below any accepted bound b (extra(b) counts
+// values held elsewhere, e.g. a running list).  Bisection on the value (all
+// values are >= 0) keeps that property and stops once at most `cap` values
+// of s lie below the bound; returns the bound, or -1 when it cannot get there
+// (more than `cap` values tie).  Used where the threshold taken from lane
+// minima is loose: at large E the distances concentrate and the (E+2)-th
+// smallest lane minimum can lie above half of all values.
+template <int CH, class Extra>
+__device__ __forceinline__ float shrink_bound(const float (&s)[CH], float hi, int c_hi, int need,
+                                              int cap, Extra extra) {
+    float lo = 0.f;
+    for (int it = 0; it < 48 && c_hi > cap; ++it) {
+        const float mid = 0.5f * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;  // no float left between the two
+        const int cm = warp_count_le<CH>(s, mid);
+        if (cm + extra(mid) >= need) {
+            hi = mid;
+            c_hi = cm;
+        } else {
+            lo = mid;
+        }
+    }
+    return c_hi <= cap ? hi : -1.f;
+}
+
 // The K nearest candidates (exact FP64 neighbour set) of the query time t
 // from the FP32 squared distances held in registers: s[j] is the distance to
 // the candidate u = lane + 32 j, +inf when u is not a candidate.  Steps as in
@@ -402,6 +440,11 @@ __device__ __forceinline__ void select_set_regs(const float (&s)[CH], const floa
         __syncwarp();
         c = base;
     }
+    if (c > KNN_CAP) {
+        // a loose threshold: shrink it so that the values under it fit
+        const float b = shrink_bound<CH>(s, theta, c, R, KNN_CAP, [](float) { return 0; });
+        if (b >= 0.f) c = compact_le<CH>(s, b, ws);
+    }
     if (c <= KNN_CAP) {
         rank_keys(ws, c, R);
         const float edge = band_edge(key_s(ws->sel[K - 1]), E);
@@ -421,7 +464,7 @@ __device__ __forceinline__ void select_set_regs(const float (&s)[CH], const floa
         else
             brute_fp64(xs, t, lo, hi, E, tau, ws, K);
     } else {
-        // more than KNN_CAP values tie at the bound (long runs of repeats)
+        // more than KNN_CAP values tie (long runs of repeats)
         brute_fp64(xs, t, lo, hi, E, tau, ws, K);
     }
     if (lane < K) {

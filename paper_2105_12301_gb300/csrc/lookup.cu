@@ -44,11 +44,17 @@ constexpr int LK_TILE_ROW = 128;               // bytes per time row of a tile
 
 // ---------------------------------------------------------- target store
 
-__global__ void target_mean_kernel(const float *__restrict__ Y, long long ld, int N, int L,
+// Row r of the target store is series rows[r] of Y (series r when rows is NULL).
+__device__ __forceinline__ size_t target_row(const int32_t *rows, int r) {
+    return static_cast<size_t>(rows ? rows[r] : r);
+}
+
+__global__ void target_mean_kernel(const float *__restrict__ Y, long long ld,
+                                   const int32_t *__restrict__ rows, int N, int L,
                                    double *__restrict__ mean) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = lane_id();
     if (warp >= N) return;
-    const float *y = Y + static_cast<size_t>(warp) * ld;
+    const float *y = Y + target_row(rows, warp) * ld;
     double s = 0.0;
     for (int i = lane; i < L; i += 32) s += static_cast<double>(y[i]);
     s = warp_sum_d(s);
@@ -61,7 +67,8 @@ __global__ void target_mean_kernel(const float *__restrict__ Y, long long ld, in
 // Every tile has L+1 time rows; row L is all zeros (the dummy neighbour row
 // of odd-length tables).
 template <bool BF16>
-__global__ void target_store_kernel(const float *__restrict__ Y, long long ld, int N, int L,
+__global__ void target_store_kernel(const float *__restrict__ Y, long long ld,
+                                    const int32_t *__restrict__ rows, int N, int L,
                                     const double *__restrict__ mean, uint8_t *__restrict__ Yt) {
     constexpr int TT = BF16 ? 64 : 32;  // targets per tile
     __shared__ float s[TT][33];
@@ -71,7 +78,7 @@ __global__ void target_store_kernel(const float *__restrict__ Y, long long ld, i
         const int tgt = tile * TT + j, u = u0 + tx;
         float v = 0.f;
         if (tgt < N && u < L)
-            v = static_cast<float>(static_cast<double>(Y[static_cast<size_t>(tgt) * ld + u]) -
+            v = static_cast<float>(static_cast<double>(Y[target_row(rows, tgt) * ld + u]) -
                                    mean[tgt]);
         s[j][tx] = v;
     }
@@ -149,12 +156,12 @@ size_t target_store_bytes(int N_tgt, int L, edm_precision prec) {
     return align_up(tiles * (L + 1) * LK_TILE_ROW, 256);
 }
 
-edm_status launch_target_store(edm_ctx *ctx, const float *Y, long long ld, int N_tgt, int L,
-                               int tau, int Tp, edm_precision prec, uint8_t *Yt, double *mean_ws,
-                               double *ysum, double *yysum) {
+edm_status launch_target_store(edm_ctx *ctx, const float *Y, long long ld, const int32_t *rows,
+                               int N_tgt, int L, int tau, int Tp, edm_precision prec, uint8_t *Yt,
+                               double *mean_ws, double *ysum, double *yysum) {
     const int warps_blocks = (N_tgt * 32 + 255) / 256;
     before_launch(ctx);
-    target_mean_kernel<<<warps_blocks, 256, 0, ctx->stream>>>(Y, ld, N_tgt, L, mean_ws);
+    target_mean_kernel<<<warps_blocks, 256, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean_ws);
     edm_status st = after_launch(ctx, "target_mean_kernel");
     if (st != EDM_OK) return st;
     const int tt = targets_per_tile(prec);
@@ -162,9 +169,9 @@ edm_status launch_target_store(edm_ctx *ctx, const float *Y, long long ld, int N
     const bool bf16 = prec == EDM_BF16_TARGETS;
     before_launch(ctx);
     if (bf16)
-        target_store_kernel<true><<<grid, block, 0, ctx->stream>>>(Y, ld, N_tgt, L, mean_ws, Yt);
+        target_store_kernel<true><<<grid, block, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean_ws, Yt);
     else
-        target_store_kernel<false><<<grid, block, 0, ctx->stream>>>(Y, ld, N_tgt, L, mean_ws, Yt);
+        target_store_kernel<false><<<grid, block, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean_ws, Yt);
     st = after_launch(ctx, "target_store_kernel");
     if (st != EDM_OK) return st;
     before_launch(ctx);
@@ -188,8 +195,13 @@ struct LookupArgs {
     int stages, stage_bytes;
     float *rho;
     long long rho_ld;
+    const int32_t *rho_col;  // column of target tgt in rho (tgt itself when NULL)
     int *flags;
 };
+
+__device__ __forceinline__ long long rho_column(const LookupArgs &a, int tgt) {
+    return a.rho_col ? a.rho_col[tgt] : tgt;
+}
 
 // Per-lane prediction moments of one library: for each of the lane's
 // targets, the sums of the prediction, of its square and of its product with
@@ -377,7 +389,7 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
                     float *rho_row = a.rho + static_cast<long long>(libs[m] - a.lib0) * a.rho_ld;
                     for (int j = lane; j < TT; j += 32) {
                         const int tgt = tile_id * TT + j;
-                        if (tgt < a.N_tgt) rho_row[tgt] = __int_as_float(0x7fc00000);
+                        if (tgt < a.N_tgt) rho_row[rho_column(a, tgt)] = __int_as_float(0x7fc00000);
                     }
                 }
                 if (lane == 0 && blockIdx.x == 0) set_flag(a.flags, EDMF_BADARG);
@@ -406,16 +418,17 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
                 if (!BF16) {
                     const int tgt = tile_id * 32 + lane;
                     if (tgt < a.N_tgt)
-                        rho_row[tgt] = finish_rho(dn, S[m][0], S[m][1], S[m][2], a.ysum[wo + tgt],
-                                                  a.yysum[wo + tgt]);
+                        rho_row[rho_column(a, tgt)] = finish_rho(dn, S[m][0], S[m][1], S[m][2],
+                                                                 a.ysum[wo + tgt], a.yysum[wo + tgt]);
                 } else {
                     const int tgt = tile_id * 64 + 2 * lane;
                     if (tgt < a.N_tgt)
-                        rho_row[tgt] = finish_rho(dn, S[m][0], S[m][1], S[m][2], a.ysum[wo + tgt],
-                                                  a.yysum[wo + tgt]);
+                        rho_row[rho_column(a, tgt)] = finish_rho(dn, S[m][0], S[m][1], S[m][2],
+                                                                 a.ysum[wo + tgt], a.yysum[wo + tgt]);
                     if (tgt + 1 < a.N_tgt)
-                        rho_row[tgt + 1] = finish_rho(dn, S[m][3], S[m][4], S[m][5],
-                                                      a.ysum[wo + tgt + 1], a.yysum[wo + tgt + 1]);
+                        rho_row[rho_column(a, tgt + 1)] =
+                            finish_rho(dn, S[m][3], S[m][4], S[m][5], a.ysum[wo + tgt + 1],
+                                       a.yysum[wo + tgt + 1]);
                 }
             }
             ++done;
@@ -508,7 +521,7 @@ uint64_t lookup_bucket(int L, int N_tgt, int nlib, edm_precision prec) {
 edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, const uint8_t *tables,
                          const CcmGroups &g, int lib0, int nlib, int tau, int Tp,
                          edm_precision prec, const double *ysum, const double *yysum, float *rho,
-                         long long rho_ld) {
+                         long long rho_ld, const int32_t *rho_col) {
     const bool bf16 = prec == EDM_BF16_TARGETS;
     const int tt = targets_per_tile(prec);
     const int n_tiles = (N_tgt + tt - 1) / tt;
@@ -556,6 +569,7 @@ edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, cons
     a.stage_bytes = static_cast<int>(stage_bytes);
     a.rho = rho;
     a.rho_ld = rho_ld;
+    a.rho_col = rho_col;
     a.flags = ctx->d_flags;
     dim3 grid(n_tiles, static_cast<unsigned>((g.ngroups_max + GB - 1) / GB));
     void (*kern)(const LookupArgs);

@@ -297,7 +297,17 @@ __device__ void sweep_long_row(const float *xs, int L, int t, int hi, int E_max,
                 bound = fminf(bound, warp_sorted_at_f(lmin, min(R, 32) - 1));
             }
             if (__shfl_sync(FULL, degen, E - 1)) continue;
-            const int c = compact_le<LS_CH>(s, bound, ws, c0);
+            int c = compact_le<LS_CH>(s, bound, ws, c0);
+            if (c > KNN_CAP - 32) {
+                // a loose bound (large E, first chunks): shrink it while the
+                // chunk's values under it plus the list's still number >= R
+                auto in_list = [&](float b) {
+                    const bool p = lane < have && key_s(list[lane]) <= b;
+                    return __popc(__ballot_sync(FULL, p));
+                };
+                const float b = shrink_bound<LS_CH>(s, bound, c, R, KNN_CAP - 32, in_list);
+                if (b >= 0.f) c = compact_le<LS_CH>(s, b, ws, c0);
+            }
             if (c > KNN_CAP - 32) {
                 // more values tie at the bound than the buffer holds (long
                 // runs of repeated values): this E is resolved in FP64 below

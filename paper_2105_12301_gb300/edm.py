@@ -78,6 +78,7 @@ def load():
     lib.edm_simplex_optimal_E_noalloc.argtypes = [vp, ci, ci, ci, ci, ci, vp, vp, vp]
     lib.edm_check_wait_timeout.argtypes = [vp, ci]
     lib.edm_predict.argtypes = [vp, vp, ci, vp, ci, ci, vp, vp, ci, ci, vp]
+    lib.edm_ccm_all_target_E.argtypes = [vp, vp, ci, vp, ci, ci, vp, ci, ci, ci, vp]
     lib.edm_profile_enable.argtypes = [vp, ci]
     lib.edm_profile_read.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ci)]
@@ -88,7 +89,7 @@ def load():
               "edm_profile_enable", "edm_profile_read", "edm_probe_smem_bandwidth",
               "edm_simplex_optimal_E_noalloc", "edm_ccm_window",
               "edm_simplex_optimal_E_batched", "edm_set_option", "edm_check_wait_timeout",
-              "edm_predict"):
+              "edm_predict", "edm_ccm_all_target_E"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -263,6 +264,28 @@ def edm_ccm_all(X_lib, Y_tgt, E_lib, tau=1, Tp=0, precision="fp32", out=None):
     ctx = _ctx(X_lib.device)
     _check(ctx, load().edm_ccm_all(ctx, _ptr(X_lib), N_lib, _ptr(Y_tgt), N_tgt, L, _ptr(E_lib),
                                    tau, Tp, _prec(precision), _ptr(rho)), "edm_ccm_all")
+    return rho
+
+
+def edm_ccm_all_target_E(X_lib, Y_tgt, E_tgt, tau=1, Tp=0, precision="fp32", out=None):
+    """rho [N_lib][N_tgt] with every library embedded at each target's E
+    (E_tgt: CUDA int32 [N_tgt]); synchronises the stream once."""
+    _series(X_lib, "X_lib", 2)
+    _series(Y_tgt, "Y_tgt", 2)
+    if X_lib.shape[1] != Y_tgt.shape[1]:
+        raise ValueError("libraries and targets must have the same length")
+    N_lib, L = X_lib.shape
+    N_tgt = Y_tgt.shape[0]
+    if E_tgt.dtype != torch.int32 or not E_tgt.is_cuda or E_tgt.shape != (N_tgt,):
+        raise TypeError("E_tgt must be a CUDA int32 tensor of shape [N_tgt]")
+    rho = out if out is not None else torch.empty((N_lib, N_tgt), dtype=torch.float32,
+                                                  device=X_lib.device)
+    if rho.shape != (N_lib, N_tgt) or rho.dtype != torch.float32 or not rho.is_contiguous():
+        raise TypeError("out must be a contiguous float32 [N_lib][N_tgt] tensor")
+    ctx = _ctx(X_lib.device)
+    _check(ctx, load().edm_ccm_all_target_E(ctx, _ptr(X_lib), N_lib, _ptr(Y_tgt), N_tgt, L,
+                                            _ptr(E_tgt.contiguous()), tau, Tp, _prec(precision),
+                                            _ptr(rho)), "edm_ccm_all_target_E")
     return rho
 
 

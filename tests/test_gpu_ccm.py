@@ -234,3 +234,24 @@ def test_set_option_rejects_unknown():
         edm.edm_set_option("no_such_option", 1)
     with pytest.raises(edm.EdmError):
         edm.edm_set_option("batch_streams", 0)
+
+
+def test_per_target_E_rule_matches_oracle():
+    # section 3.3: each library is embedded at each target's E
+    X = inputs.config2(N=14, L=350)
+    Y = inputs.coupled_logistic(11, 350, 5150)
+    E_tgt = np.array([2, 1, 3, 2, 5, 20, 2, 1, 3, 7, 2], np.int32)
+    for prec, tol in (("fp32", TOL_FP32), ("bf16", TOL_BF16)):
+        rho = edm.edm_ccm_all_target_E(gpu(X), gpu(Y), gpu(E_tgt), 1, 0, prec)
+        edm.edm_ctx_sync()
+        rho = rho.cpu().numpy()
+        ref = np.stack([[oracle.ccm_row(X[i], Y[j], int(E_tgt[j]), 1, 0)[0]
+                         for j in range(Y.shape[0])] for i in range(X.shape[0])])
+        assert np.max(np.abs(rho - ref)) <= tol
+    # a single E equals the per-library call with that E everywhere
+    E3 = np.full(Y.shape[0], 3, np.int32)
+    a = edm.edm_ccm_all_target_E(gpu(X), gpu(Y), gpu(E3), 1, 0, "fp32")
+    b = edm.edm_ccm_all(gpu(X), gpu(Y), gpu(np.full(X.shape[0], 3, np.int32)), 1, 0, "fp32")
+    torch.testing.assert_close(a, b, rtol=0, atol=0)
+    with pytest.raises(edm.EdmError):
+        edm.edm_ccm_all_target_E(gpu(X), gpu(Y), gpu(np.full(Y.shape[0], 21, np.int32)))
