@@ -350,6 +350,46 @@ __device__ __forceinline__ int compact_le(const float (&s)[CH], float bound, War
 }
 
 
+// Compact the keys (s[j], u0+lane+32j) with s[j] <= bound, a FINITE bound,
+// into ws->key, visiting only the slot groups (4 slots each, minima in gm)
+// in which some lane holds such a value; returns how many there are (only
+// the first KNN_CAP are stored).  Finite bounds exclude the +inf
+// non-candidates by themselves.
+template <int CH>
+__device__ __forceinline__ int compact_le_groups(const float (&s)[CH], const float (&gm)[CH / 4],
+                                                 float bound, WarpScratch *ws, int u0 = 0) {
+    const int lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    int base = 0;
+#pragma unroll
+    for (int g = 0; g < CH / 4; ++g) {
+        if (__any_sync(FULL, gm[g] <= bound)) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int j = 4 * g + i;
+                const bool p = s[j] <= bound;
+                const unsigned b = __ballot_sync(FULL, p);
+                if (p) {
+                    const int pos = base + __popc(b & lt);
+                    if (pos < KNN_CAP) ws->key[pos] = mk_key(s[j], u0 + lane + 32 * j);
+                }
+                base += __popc(b);
+            }
+        }
+    }
+    __syncwarp();
+    return base;
+}
+
+// Minima of the 4-slot groups of a register array.
+template <int CH>
+__device__ __forceinline__ void group_minima(const float (&s)[CH], float (&gm)[CH / 4]) {
+    static_assert(CH % 4 == 0, "slots come in groups of four");
+#pragma unroll
+    for (int g = 0; g < CH / 4; ++g)
+        gm[g] = fminf(fminf(s[4 * g], s[4 * g + 1]), fminf(s[4 * g + 2], s[4 * g + 3]));
+}
+
 // Warp-wide number of register slots with s <= b.
 template <int CH>
 __device__ __forceinline__ int warp_count_le(const float (&s)[CH], float b) {
@@ -399,51 +439,24 @@ template <int CH>
 __device__ __forceinline__ void select_set_regs(const float (&s)[CH], const float *xs, int t,
                                                 int lo, int hi, int E, int tau, int K,
                                                 WarpScratch *ws, int &u_out, float &d_out) {
-    static_assert(CH % 4 == 0, "slots come in groups of four");
     constexpr int NG = CH / 4;
     const int lane = lane_id();
     const int nc = hi - lo;
     const int R = min(K + 1, nc);
     // minima of the slot groups (4 slots each) and of the lane
     float gm[NG];
-#pragma unroll
-    for (int g = 0; g < NG; ++g)
-        gm[g] = fminf(fminf(s[4 * g], s[4 * g + 1]), fminf(s[4 * g + 2], s[4 * g + 3]));
+    group_minima<CH>(s, gm);
     float lmin = EDM_INF;
 #pragma unroll
     for (int g = 0; g < NG; ++g) lmin = fminf(lmin, gm[g]);
     const float theta = warp_sorted_at_f(lmin, R - 1);
-    int c;
-    if (theta == EDM_INF) {
-        c = compact_le<CH>(s, theta, ws);
-    } else {
-        // theta is finite, so s <= theta excludes the +inf non-candidates;
-        // only slot groups in which some lane holds such a value are visited
-        const unsigned lt = (1u << lane) - 1u;
-        int base = 0;
-#pragma unroll
-        for (int g = 0; g < NG; ++g) {
-            if (__any_sync(FULL, gm[g] <= theta)) {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int j = 4 * g + i;
-                    const bool p = s[j] <= theta;
-                    const unsigned b = __ballot_sync(FULL, p);
-                    if (p) {
-                        const int pos = base + __popc(b & lt);
-                        if (pos < KNN_CAP) ws->key[pos] = mk_key(s[j], lane + 32 * j);
-                    }
-                    base += __popc(b);
-                }
-            }
-        }
-        __syncwarp();
-        c = base;
-    }
+    // a finite theta excludes the +inf non-candidates by itself
+    int c = theta == EDM_INF ? compact_le<CH>(s, theta, ws)
+                             : compact_le_groups<CH>(s, gm, theta, ws);
     if (c > KNN_CAP) {
         // a loose threshold: shrink it so that the values under it fit
         const float b = shrink_bound<CH>(s, theta, c, R, KNN_CAP, [](float) { return 0; });
-        if (b >= 0.f) c = compact_le<CH>(s, b, ws);
+        if (b >= 0.f) c = compact_le_groups<CH>(s, gm, b, ws);
     }
     if (c <= KNN_CAP) {
         rank_keys(ws, c, R);

@@ -256,6 +256,85 @@ struct LongScratch {
     uint64_t list[LS_LIST];   // per E: its R smallest keys so far, ascending
 };
 
+// One chunk of 32*LS_CH candidates u = c0 + lane + 32 j for every E of the
+// row.  In an interior chunk every candidate is a point of every P_E
+// (c0 >= (E_row-1)tau and the chunk ends at or before hi), so the lagged
+// reads need no clamp and no candidate leaves the set; only that update
+// loop differs (a warp-uniform branch), the selection code is shared.
+__device__ __forceinline__ void long_chunk(const float *xs, int L, int t, int hi, int E_row,
+                                           int tau, int c0, bool interior, LongScratch *sc,
+                                           int &cnt, int &degen) {
+    const int lane = lane_id();
+    WarpScratch *ws = &sc->ws;
+    float s[LS_CH];
+#pragma unroll
+    for (int j = 0; j < LS_CH; ++j) {
+        const int u = c0 + lane + 32 * j;
+        s[j] = u <= hi && u != t ? 0.f : EDM_INF;
+    }
+    for (int E = 1; E <= E_row; ++E) {
+        const int lo = (E - 1) * tau;
+        const float qv = xs[t - lo];
+        if (interior) {
+            const float *xl = xs + (c0 + lane - lo);
+#pragma unroll
+            for (int j = 0; j < LS_CH; ++j) {
+                const float d = __fsub_rn(qv, xl[32 * j]);
+                s[j] = __fmaf_rn(d, d, s[j]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < LS_CH; ++j) {
+                const int u = c0 + lane + 32 * j;
+                const float d = __fsub_rn(qv, xs[min(max(u - lo, 0), L - 1)]);
+                const float v = __fmaf_rn(d, d, s[j]);
+                s[j] = (u < lo) ? EDM_INF : v;
+            }
+        }
+        const int R = min(E + 2, hi - lo);
+        uint64_t *list = sc->list + ls_list_off(E);
+        const int have = __shfl_sync(FULL, cnt, E - 1);
+        if (__shfl_sync(FULL, degen, E - 1)) continue;
+        float gm[LS_CH / 4];
+        group_minima<LS_CH>(s, gm);
+        float bound = have == R ? key_s(list[R - 1]) : EDM_INF;
+        if (have < R) {
+            float lmin = EDM_INF;
+#pragma unroll
+            for (int g = 0; g < LS_CH / 4; ++g) lmin = fminf(lmin, gm[g]);
+            bound = fminf(bound, warp_sorted_at_f(lmin, min(R, 32) - 1));
+        }
+        int c = bound == EDM_INF ? compact_le<LS_CH>(s, bound, ws, c0)
+                                 : compact_le_groups<LS_CH>(s, gm, bound, ws, c0);
+        if (c > KNN_CAP - 32) {
+            // a loose bound (large E, first chunks): shrink it while the
+            // chunk's values under it plus the list's still number >= R
+            auto in_list = [&](float b) {
+                const bool p = lane < have && key_s(list[lane]) <= b;
+                return __popc(__ballot_sync(FULL, p));
+            };
+            const float b = shrink_bound<LS_CH>(s, bound, c, R, KNN_CAP - 32, in_list);
+            if (b >= 0.f) c = compact_le_groups<LS_CH>(s, gm, b, ws, c0);
+        }
+        if (c > KNN_CAP - 32) {
+            // more values tie at the bound than the buffer holds (long runs
+            // of repeated values): this E is resolved in FP64 after the chunks
+            if (lane == E - 1) degen = 1;
+            continue;
+        }
+        if (c == 0) continue;
+        // merge the collected keys with the list and keep the R smallest
+        for (int e = lane; e < have; e += 32) ws->key[c + e] = list[e];
+        __syncwarp();
+        const int tot = c + have;
+        rank_keys(ws, tot, min(R, tot));
+        const int keep = min(R, tot);
+        for (int e = lane; e < keep; e += 32) list[e] = ws->sel[e];
+        __syncwarp();
+        if (lane == E - 1) cnt = keep;
+    }
+}
+
 __device__ void sweep_long_row(const float *xs, int L, int t, int hi, int E_max, int tau, int Tp,
                                float mu, LongScratch *sc, float (&m)[5]) {
     const int lane = lane_id();
@@ -269,63 +348,10 @@ __device__ void sweep_long_row(const float *xs, int L, int t, int hi, int E_max,
     }
     int cnt = 0;    // lane e: keys held in the list of E = e+1
     int degen = 0;  // lane e: E = e+1 has too many ties for the list
-    for (int c0 = 0; c0 <= hi; c0 += 32 * LS_CH) {
-        float s[LS_CH];
-#pragma unroll
-        for (int j = 0; j < LS_CH; ++j) {
-            const int u = c0 + lane + 32 * j;
-            s[j] = (u <= hi && u != t) ? 0.f : EDM_INF;
-        }
-        for (int E = 1; E <= E_row; ++E) {
-            const int lo = (E - 1) * tau;
-            const float qv = xs[t - lo];
-#pragma unroll
-            for (int j = 0; j < LS_CH; ++j) {
-                const int u = c0 + lane + 32 * j;
-                const float d = __fsub_rn(qv, xs[min(max(u - lo, 0), L - 1)]);
-                const float v = __fmaf_rn(d, d, s[j]);
-                s[j] = (u < lo) ? EDM_INF : v;
-            }
-            const int R = min(E + 2, hi - lo);
-            uint64_t *list = sc->list + ls_list_off(E);
-            const int have = __shfl_sync(FULL, cnt, E - 1);
-            float bound = have == R ? key_s(list[R - 1]) : EDM_INF;
-            if (have < R) {
-                float lmin = EDM_INF;
-#pragma unroll
-                for (int j = 0; j < LS_CH; ++j) lmin = fminf(lmin, s[j]);
-                bound = fminf(bound, warp_sorted_at_f(lmin, min(R, 32) - 1));
-            }
-            if (__shfl_sync(FULL, degen, E - 1)) continue;
-            int c = compact_le<LS_CH>(s, bound, ws, c0);
-            if (c > KNN_CAP - 32) {
-                // a loose bound (large E, first chunks): shrink it while the
-                // chunk's values under it plus the list's still number >= R
-                auto in_list = [&](float b) {
-                    const bool p = lane < have && key_s(list[lane]) <= b;
-                    return __popc(__ballot_sync(FULL, p));
-                };
-                const float b = shrink_bound<LS_CH>(s, bound, c, R, KNN_CAP - 32, in_list);
-                if (b >= 0.f) c = compact_le<LS_CH>(s, b, ws, c0);
-            }
-            if (c > KNN_CAP - 32) {
-                // more values tie at the bound than the buffer holds (long
-                // runs of repeated values): this E is resolved in FP64 below
-                if (lane == E - 1) degen = 1;
-                continue;
-            }
-            if (c == 0) continue;
-            // merge the collected keys with the list and keep the R smallest
-            for (int e = lane; e < have; e += 32) ws->key[c + e] = list[e];
-            __syncwarp();
-            const int tot = c + have;
-            rank_keys(ws, tot, min(R, tot));
-            const int keep = min(R, tot);
-            for (int e = lane; e < keep; e += 32) list[e] = ws->sel[e];
-            __syncwarp();
-            if (lane == E - 1) cnt = keep;
-        }
-    }
+    const int lo_max = (E_row - 1) * tau;
+    for (int c0 = 0; c0 <= hi; c0 += 32 * LS_CH)
+        long_chunk(xs, L, t, hi, E_row, tau, c0, c0 >= lo_max && c0 + 32 * LS_CH - 1 <= hi, sc,
+                   cnt, degen);
     // every E now holds its exact FP32 top-R: band check, weights, moments
     for (int E = 1; E <= E_row; ++E) {
         const int lo = (E - 1) * tau, K = E + 1;
