@@ -427,16 +427,21 @@ def run_libsweep_workload(args):
     E_full, _ = edm.edm_simplex_optimal_E(Xg, E_MAX, TAU, TP_SEL, with_rho=False)
     rho = torch.empty((N, N), dtype=torch.float32, device=dev)
     sizes = {}
+    kernels = ("ccm_table_kernel", "lookup_kernel", "group_libs_kernel", "target_store_kernel")
     for L_lib in (100, 300, 1000, 3000, 10000):
         for prec in ("fp32", "bf16"):
             def one():
                 edm.edm_ccm_window(Xg, 0, L_lib, E_full, TAU, TP, prec, out=rho)
             one()
             ms = sync_time(one, dev, stream, max(1, args.steps))
+            edm.edm_profile_enable(True, dev)
+            one()
+            split = {k: edm.edm_profile_read(k, dev)[0] for k in kernels}
+            edm.edm_profile_enable(False, dev)
             edm.edm_ctx_sync(dev)
             sizes.setdefault(str(L_lib), {})[prec] = {"value": N * N / (ms / 1e3),
-                                                      "ms": ms}
-            log("window %d %s %.1f ms" % (L_lib, prec, ms))
+                                                      "ms": ms, "kernel_ms": split}
+            log("window %d %s %.1f ms %s" % (L_lib, prec, ms, split))
     out = {"metric": METRIC, "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
            "data": "synthetic", "value": sizes["10000"]["fp32"]["value"],
            "config": {"workload": "library-length sweep, %d coupled-logistic series x %d steps, "

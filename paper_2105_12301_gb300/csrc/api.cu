@@ -111,7 +111,7 @@ static int ccm_chunk(edm_ctx *ctx, int N_lib, size_t slot, int G) {
 
 static size_t ccm_workspace_bytes(edm_ctx *ctx, int N_lib, int N_tgt, int L, int tau, int Tp,
                                   edm_precision prec) {
-    const size_t yt_bytes = target_store_bytes(N_tgt, L, prec);
+    const size_t yt_bytes = target_store_bytes(N_tgt, L, prec, lookup_row_words(ctx, L, prec));
     const size_t mean_bytes = align_up(sizeof(double) * N_tgt, 256);
     const size_t sums_bytes = align_up(sizeof(double) * N_tgt * EDM_E_MAX, 256);
     const size_t slot = ccm_slot_bytes(L, tau, Tp);
@@ -131,7 +131,8 @@ static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, in
                           const int32_t *E_lib, int E_uniform, int tau, int Tp, edm_precision prec,
                           float *rho, long long rho_ld, const int32_t *tgt_rows,
                           const int32_t *rho_cols) {
-    const size_t yt_bytes = target_store_bytes(N_tgt, L, prec);
+    const int rw = lookup_row_words(ctx, L, prec);
+    const size_t yt_bytes = target_store_bytes(N_tgt, L, prec, rw);
     const size_t mean_bytes = align_up(sizeof(double) * N_tgt, 256);
     const size_t sums_bytes = align_up(sizeof(double) * N_tgt * EDM_E_MAX, 256);
     const size_t slot = ccm_slot_bytes(L, tau, Tp);
@@ -147,7 +148,7 @@ static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, in
     double *yysum = reinterpret_cast<double *>(base + yt_bytes + mean_bytes + sums_bytes);
     uint8_t *gmem = base + yt_bytes + mean_bytes + 2 * sums_bytes;
     uint8_t *tables = gmem + groups_bytes(chunk, G);
-    st = launch_target_store(ctx, Y_tgt, ld_tgt, tgt_rows, N_tgt, L, tau, Tp, prec, Yt, mean,
+    st = launch_target_store(ctx, Y_tgt, ld_tgt, tgt_rows, N_tgt, L, tau, Tp, prec, rw, Yt, mean,
                              ysum, yysum);
     if (st != EDM_OK) return st;
     for (int c0 = 0; c0 < N_lib; c0 += chunk) {
@@ -157,8 +158,8 @@ static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, in
         if (st != EDM_OK) return st;
         st = launch_ccm_tables(ctx, X_lib, ld_lib, nlib, L, tau, Tp, grp, tables);
         if (st != EDM_OK) return st;
-        st = launch_lookup(ctx, Yt, N_tgt, L, tables, grp, c0, nlib, tau, Tp, prec, ysum, yysum,
-                           rho + static_cast<size_t>(c0) * rho_ld, rho_ld, rho_cols);
+        st = launch_lookup(ctx, Yt, N_tgt, L, tables, grp, c0, nlib, tau, Tp, prec, rw, ysum,
+                           yysum, rho + static_cast<size_t>(c0) * rho_ld, rho_ld, rho_cols);
         if (st != EDM_OK) return st;
     }
     return EDM_OK;

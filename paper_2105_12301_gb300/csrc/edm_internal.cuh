@@ -142,16 +142,22 @@ edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max,
 // of the stored values and of their squares over the observation window of
 // E (times (E-1)tau+Tp .. L-1): ysum / yysum [EDM_E_MAX][N_tgt].
 // Y: target series with row stride ld (>= L) floats; target r of the store is
-// series rows[r] (series r when rows is NULL).
+// series rows[r] (series r when rows is NULL).  rw: 32-bit words per tile
+// row (lookup_row_words).
 edm_status launch_target_store(edm_ctx *ctx, const float *Y, long long ld, const int32_t *rows,
-                               int N_tgt, int L, int tau, int Tp, edm_precision prec, uint8_t *Yt,
-                               double *mean_ws, double *ysum, double *yysum);
+                               int N_tgt, int L, int tau, int Tp, edm_precision prec, int rw,
+                               uint8_t *Yt, double *mean_ws, double *ysum, double *yysum);
+// Words per target-tile row for series of length L: 32 (128-byte rows) when
+// such a tile fits a CTA's shared memory or nothing smaller does, 16 when
+// only the half-width tile fits.
+int lookup_row_words(edm_ctx *ctx, int L, edm_precision prec);
 // rho points at the row of library lib0; row of library i = rho + (i - lib0) * rho_ld;
 // stored target r goes to column rho_col[r] (column r when rho_col is NULL).
 edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L,
                          const uint8_t *tables, const CcmGroups &g, int lib0, int nlib, int tau,
-                         int Tp, edm_precision prec, const double *ysum, const double *yysum,
-                         float *rho, long long rho_ld, const int32_t *rho_col);
+                         int Tp, edm_precision prec, int rw, const double *ysum,
+                         const double *yysum, float *rho, long long rho_ld,
+                         const int32_t *rho_col);
 // Predictions of libraries lib0.. (groups g, tables built by launch_ccm_tables)
 // for their targets Y[tgt_of[lib]] (Y[lib] when tgt_of is NULL).
 edm_status launch_predict(edm_ctx *ctx, const float *Y, long long ld_tgt, int N_tgt,
@@ -164,7 +170,7 @@ size_t simplex_workspace_bytes(edm_ctx *ctx, int N, int L, int E_max);
 uint64_t lookup_bucket(int L, int N_tgt, int nlib, edm_precision prec);
 int lookup_default_lb(edm_ctx *ctx, int nlib, int n_tiles);
 size_t ccm_slot_bytes(int L, int tau, int Tp);
-size_t target_store_bytes(int N_tgt, int L, edm_precision prec);
+size_t target_store_bytes(int N_tgt, int L, edm_precision prec, int rw);
 
 // --------------------------------------------------------------- device side
 

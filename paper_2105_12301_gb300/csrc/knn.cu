@@ -150,23 +150,6 @@ __device__ __forceinline__ void write_table_row(uint8_t *slot, size_t pair_strid
         block[2 * lane + 1] = lane < K - 1 ? 0u : (static_cast<uint32_t>(L) | (static_cast<uint32_t>(L) << 16));
 }
 
-// Rows [r0, r1) of one library's table: the exact FP64 neighbour set,
-// normalised simplex weights, neighbour rows pre-shifted by Tp.
-template <int E>
-__device__ __forceinline__ void table_rows(const float *xs, int L, int tau, int Tp, int r0, int r1,
-                                           WarpScratch *ws, uint8_t *slot, size_t pair_stride) {
-    constexpr int K = E + 1;
-    const int lo = (E - 1) * tau, hi = L - 1 - Tp, n = hi - lo + 1;
-    const int warp = threadIdx.x >> 5;
-    for (int i = r0 + warp; i < r1; i += KNN_WARPS) {
-        int u = 0;
-        float d = 0.f;
-        knn_row<E, KNN_SET>(xs, lo + i, lo, hi, tau, K, ws, &u, &d);
-        const float w = simplex_weight(d, K);
-        write_table_row(slot, pair_stride, i, n, K, L, Tp, u, w);
-    }
-}
-
 // The library of group slot s (blockIdx.x), its E, where its table starts and
 // the distance between its consecutive pair blocks.  False for an empty slot
 // or a library whose E is invalid (its group has E = 0; the lookup writes its
@@ -188,33 +171,6 @@ __device__ __forceinline__ bool table_slot(const CcmGroups &g, uint8_t *tables, 
     ts.base = tables + g.off[grp] + m * pb;
     ts.pair_stride = pb * g.G;
     return true;
-}
-
-template <bool SMEM>
-__global__ void __launch_bounds__(KNN_WARPS * 32)
-    ccm_table_kernel(const float *__restrict__ X, long long ld, int L, int tau, int Tp, int RB,
-                     const CcmGroups g, uint8_t *__restrict__ tables) {
-    extern __shared__ __align__(16) uint8_t smem[];
-    WarpScratch *wsa = reinterpret_cast<WarpScratch *>(smem);
-    float *xs_s = reinterpret_cast<float *>(smem + KNN_WARPS * sizeof(WarpScratch));
-    TableSlot ts;
-    if (!table_slot(g, tables, ts)) return;
-    const int E = ts.E;
-    const int n = L - (E - 1) * tau - Tp;
-    const int r0 = blockIdx.y * RB, r1 = min(n, r0 + RB);
-    if (r0 >= r1) return;
-    const float *xs = stage_series<SMEM>(X + static_cast<size_t>(ts.lib) * ld, L, xs_s);
-    WarpScratch *ws = wsa + (threadIdx.x >> 5);
-    switch (E) {
-#define EDM_CASE(e) \
-    case e: table_rows<e>(xs, L, tau, Tp, r0, r1, ws, ts.base, ts.pair_stride); break;
-        EDM_CASE(1) EDM_CASE(2) EDM_CASE(3) EDM_CASE(4) EDM_CASE(5) EDM_CASE(6) EDM_CASE(7)
-        EDM_CASE(8) EDM_CASE(9) EDM_CASE(10) EDM_CASE(11) EDM_CASE(12) EDM_CASE(13)
-        EDM_CASE(14) EDM_CASE(15) EDM_CASE(16) EDM_CASE(17) EDM_CASE(18) EDM_CASE(19)
-        EDM_CASE(20)
-#undef EDM_CASE
-    default: break;
-    }
 }
 
 // Register-resident variant for series of up to 32*CH points: the FP32
@@ -269,6 +225,164 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
     }
 }
 
+// ------------------------------------------- tables of long series (> 2,048)
+
+constexpr int TL_CH = 32;  // candidate slots per lane per chunk (1,024 candidates)
+
+struct TableLongScratch {
+    WarpScratch ws;
+    uint64_t list[32];  // the R = k+1 smallest FP32 keys seen so far, ascending
+};
+
+// The k = E+1 nearest neighbours (exact FP64 set) of the query time t among
+// the times lo..hi, from chunks of 1,024 candidates whose FP32 squared
+// distances are accumulated in registers (lag order 0..E-1, one fma per lag,
+// the same operations as dist32).  Each chunk is selected against a running
+// list of the R smallest keys, as in the long optimal-E sweep; then the FP64
+// band check of knn_row's KNN_SET mode.  On return lane r < K holds the r-th
+// neighbour and its distance.
+__device__ void table_row_long(const float *xs, int L, int t, int lo, int hi, int E, int tau,
+                               TableLongScratch *sc, int &u_out, float &d_out) {
+    const int lane = lane_id();
+    WarpScratch *ws = &sc->ws;
+    uint64_t *list = sc->list;
+    const int K = E + 1;
+    const int R = min(K + 1, hi - lo);
+    int have = 0;
+    bool deg = false;
+    for (int c0 = 0; c0 <= hi; c0 += 32 * TL_CH) {
+        float s[TL_CH];
+        if (c0 >= lo && c0 + 32 * TL_CH - 1 <= hi) {
+            // every candidate is a point of P: no clamp, only t itself is out
+            const float *xl = xs + (c0 + lane);
+#pragma unroll
+            for (int j = 0; j < TL_CH; ++j) s[j] = (c0 + lane + 32 * j == t) ? EDM_INF : 0.f;
+            for (int l = 0; l < E; ++l) {
+                const float q = xs[t - l * tau];
+                const float *xo = xl - l * tau;
+#pragma unroll
+                for (int j = 0; j < TL_CH; ++j) {
+                    const float d = __fsub_rn(q, xo[32 * j]);
+                    s[j] = __fmaf_rn(d, d, s[j]);
+                }
+            }
+        } else {
+            // non-candidates start at +inf and stay there (fma(d, d, inf) = inf)
+#pragma unroll
+            for (int j = 0; j < TL_CH; ++j) {
+                const int u = c0 + lane + 32 * j;
+                s[j] = (u >= lo && u <= hi && u != t) ? 0.f : EDM_INF;
+            }
+            for (int l = 0; l < E; ++l) {
+                const float q = xs[t - l * tau];
+#pragma unroll
+                for (int j = 0; j < TL_CH; ++j) {
+                    const int u = c0 + lane + 32 * j;
+                    const float d = __fsub_rn(q, xs[min(max(u - l * tau, 0), L - 1)]);
+                    s[j] = __fmaf_rn(d, d, s[j]);
+                }
+            }
+        }
+        if (deg) continue;
+        float gm[TL_CH / 4];
+        group_minima<TL_CH>(s, gm);
+        float bound = have == R ? key_s(list[R - 1]) : EDM_INF;
+        if (have < R) {
+            float lmin = EDM_INF;
+#pragma unroll
+            for (int g = 0; g < TL_CH / 4; ++g) lmin = fminf(lmin, gm[g]);
+            bound = fminf(bound, warp_sorted_at_f(lmin, min(R, 32) - 1));
+        }
+        int c = bound == EDM_INF ? compact_le<TL_CH>(s, bound, ws, c0)
+                                 : compact_le_groups<TL_CH>(s, gm, bound, ws, c0);
+        if (c > KNN_CAP - 32) {
+            auto in_list = [&](float b) {
+                const bool p = lane < have && key_s(list[lane]) <= b;
+                return __popc(__ballot_sync(FULL, p));
+            };
+            const float b = shrink_bound<TL_CH>(s, bound, c, R, KNN_CAP - 32, in_list);
+            if (b >= 0.f) c = compact_le_groups<TL_CH>(s, gm, b, ws, c0);
+        }
+        if (c > KNN_CAP - 32) {
+            deg = true;  // more values tie than the buffer holds: FP64 below
+            continue;
+        }
+        if (c == 0) continue;
+        for (int e = lane; e < have; e += 32) ws->key[c + e] = list[e];
+        __syncwarp();
+        const int tot = c + have;
+        rank_keys(ws, tot, min(R, tot));
+        have = min(R, tot);
+        for (int e = lane; e < have; e += 32) list[e] = ws->sel[e];
+        __syncwarp();
+    }
+    if (!deg) {
+        const float edge = band_edge(key_s(list[K - 1]), E);
+        if (R <= K || key_s(list[K]) > edge) {
+            if (lane < K) {
+                u_out = key_u(list[lane]);
+                d_out = sqrtf(key_s(list[lane]));
+            }
+            __syncwarp();
+            return;
+        }
+        // resolve the band in FP64: every candidate with s32 <= edge
+        if (lane == 0) ws->count = 0;
+        __syncwarp();
+        for (int u = lo + lane; u <= hi; u += 32) {
+            if (u == t) continue;
+            float v = 0.f;
+            for (int l = 0; l < E; ++l) {
+                const float d = __fsub_rn(xs[t - l * tau], xs[u - l * tau]);
+                v = __fmaf_rn(d, d, v);
+            }
+            if (v <= edge) {
+                const int pos = atomicAdd(&ws->count, 1);
+                if (pos < KNN_CAP) ws->key[pos] = mk_key(v, u);
+            }
+        }
+        __syncwarp();
+        const int c = ws->count;
+        __syncwarp();
+        if (c <= KNN_CAP)
+            rank_band_fp64(xs, t, E, tau, ws, c, K);
+        else
+            brute_fp64(xs, t, lo, hi, E, tau, ws, K);
+    } else {
+        brute_fp64(xs, t, lo, hi, E, tau, ws, K);
+    }
+    if (lane < K) {
+        u_out = ws->sel_u[lane];
+        d_out = __double2float_rn(__dsqrt_rn(ws->sel_s64[lane]));
+    }
+    __syncwarp();
+}
+
+template <bool SMEM>
+__global__ void __launch_bounds__(KNN_WARPS * 32)
+    ccm_table_long_kernel(const float *__restrict__ X, long long ld, int L, int tau, int Tp,
+                          int RB, const CcmGroups g, uint8_t *__restrict__ tables) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    TableLongScratch *sca = reinterpret_cast<TableLongScratch *>(smem);
+    float *xs_s = reinterpret_cast<float *>(smem + KNN_WARPS * sizeof(TableLongScratch));
+    TableSlot ts;
+    if (!table_slot(g, tables, ts)) return;
+    const int E = ts.E;
+    const int lo = (E - 1) * tau, hi = L - 1 - Tp, n = hi - lo + 1;
+    const int r0 = blockIdx.y * RB, r1 = min(n, r0 + RB);
+    if (r0 >= r1) return;
+    const float *xs = stage_series<SMEM>(X + static_cast<size_t>(ts.lib) * ld, L, xs_s);
+    const int warp = threadIdx.x >> 5;
+    TableLongScratch *sc = sca + warp;
+    for (int i = r0 + warp; i < r1; i += KNN_WARPS) {
+        int u = 0;
+        float d = 0.f;
+        table_row_long(xs, L, lo + i, lo, hi, E, tau, sc, u, d);
+        const float w = simplex_weight(d, E + 1);
+        write_table_row(ts.base, ts.pair_stride, i, n, E + 1, L, Tp, u, w);
+    }
+}
+
 size_t ccm_slot_bytes(int L, int tau, int Tp) {
     size_t best = 0;
     for (int E = 1; E <= EDM_E_MAX; ++E) {
@@ -307,19 +421,14 @@ edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, long long ld, int nli
         kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, L, tau, Tp, RB, g, tables);
         return after_launch(ctx, "ccm_table_kernel");
     }
+    // longer series: chunks of 1,024 candidates against a running list
     const bool smem_series = sizeof(float) * static_cast<size_t>(L) <= SERIES_SMEM_MAX;
-    const size_t smem = knn_smem_bytes(smem_series, L);
-    if (smem_series) {
-        auto kern = ccm_table_kernel<true>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        before_launch(ctx);
-        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, L, tau, Tp, RB, g, tables);
-    } else {
-        auto kern = ccm_table_kernel<false>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        before_launch(ctx);
-        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, L, tau, Tp, RB, g, tables);
-    }
+    const size_t smem = KNN_WARPS * sizeof(TableLongScratch) +
+                        (smem_series ? align_up(sizeof(float) * L, 16) : 0);
+    auto kern = smem_series ? ccm_table_long_kernel<true> : ccm_table_long_kernel<false>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    before_launch(ctx);
+    kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, L, tau, Tp, RB, g, tables);
     return after_launch(ctx, "ccm_table_kernel");
 }
 

@@ -40,7 +40,6 @@ template <bool BF16> struct LkCfg {
     static constexpr int RED_FLOATS = HALF * G * NM * 32;  // hand-over buffer
 };
 constexpr int LK_MAX_STAGES = 8;
-constexpr int LK_TILE_ROW = 128;               // bytes per time row of a tile
 
 // ---------------------------------------------------------- target store
 
@@ -61,16 +60,18 @@ __global__ void target_mean_kernel(const float *__restrict__ Y, long long ld,
     if (lane == 0) mean[warp] = s / L;
 }
 
-// FP32: Yt[tile][u][32] = Y[32 tile + lane][u] - mean; pad targets are 0.
-// BF16: Yt[tile][u][64] bf16, lane l's 32-bit word holds targets 2l (low
-// half) and 2l+1 (high half), each rounded to nearest even.
-// Every tile has L+1 time rows; row L is all zeros (the dummy neighbour row
-// of odd-length tables).
-template <bool BF16>
+// A tile row holds RW 32-bit words: RW = 32 (128-byte rows) normally, 16
+// (64-byte rows) when a 32-word tile of the series length does not fit
+// shared memory but a 16-word one does.  FP32: Yt[tile][u][RW] = Y[RW tile +
+// w][u] - mean; BF16: word w holds targets 2w (low half) and 2w+1 (high
+// half), each rounded to nearest even.  Pad targets are 0.  Every tile has
+// L+1 time rows; row L is all zeros (the dummy neighbour row of odd-length
+// tables).
+template <bool BF16, int RW>
 __global__ void target_store_kernel(const float *__restrict__ Y, long long ld,
                                     const int32_t *__restrict__ rows, int N, int L,
                                     const double *__restrict__ mean, uint8_t *__restrict__ Yt) {
-    constexpr int TT = BF16 ? 64 : 32;  // targets per tile
+    constexpr int TT = BF16 ? 2 * RW : RW;  // targets per tile
     __shared__ float s[TT][33];
     const int tile = blockIdx.x, u0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
@@ -83,31 +84,32 @@ __global__ void target_store_kernel(const float *__restrict__ Y, long long ld,
         s[j][tx] = v;
     }
     __syncthreads();
-    uint8_t *base = Yt + static_cast<size_t>(tile) * (L + 1) * LK_TILE_ROW;
-    if (blockIdx.y == 0 && ty == 0)
-        reinterpret_cast<uint32_t *>(base + static_cast<size_t>(L) * LK_TILE_ROW)[tx] = 0u;
+    constexpr size_t ROW = 4 * RW;
+    uint8_t *base = Yt + static_cast<size_t>(tile) * (L + 1) * ROW;
+    if (blockIdx.y == 0 && ty == 0 && tx < RW)
+        reinterpret_cast<uint32_t *>(base + static_cast<size_t>(L) * ROW)[tx] = 0u;
+    if (tx >= RW) return;
     for (int r = ty; r < 32; r += 8) {
         const int u = u0 + r;
         if (u >= L) continue;
         if (BF16) {
             const unsigned lo = __bfloat16_as_ushort(__float2bfloat16_rn(s[2 * tx][r]));
             const unsigned hi = __bfloat16_as_ushort(__float2bfloat16_rn(s[2 * tx + 1][r]));
-            reinterpret_cast<uint32_t *>(base + static_cast<size_t>(u) * LK_TILE_ROW)[tx] =
-                lo | (hi << 16);
+            reinterpret_cast<uint32_t *>(base + static_cast<size_t>(u) * ROW)[tx] = lo | (hi << 16);
         } else {
-            reinterpret_cast<float *>(base + static_cast<size_t>(u) * LK_TILE_ROW)[tx] = s[tx][r];
+            reinterpret_cast<float *>(base + static_cast<size_t>(u) * ROW)[tx] = s[tx][r];
         }
     }
 }
 
 // The stored value of target tgt at time u, as the lookup reads it.
-template <bool BF16>
+template <bool BF16, int RW>
 __device__ __forceinline__ float stored_target(const uint8_t *Yt, int L, int tgt, int u) {
-    constexpr int TT = BF16 ? 64 : 32;
+    constexpr int TT = BF16 ? 2 * RW : RW;
     const uint32_t *row = reinterpret_cast<const uint32_t *>(
-        Yt + (static_cast<size_t>(tgt / TT) * (L + 1) + u) * LK_TILE_ROW);
-    if (!BF16) return __uint_as_float(row[tgt % 32]);
-    const uint32_t v = row[(tgt % 64) >> 1];
+        Yt + (static_cast<size_t>(tgt / TT) * (L + 1) + u) * (4 * RW));
+    if (!BF16) return __uint_as_float(row[tgt % TT]);
+    const uint32_t v = row[(tgt % TT) >> 1];
     return __uint_as_float((tgt & 1) ? (v & 0xffff0000u) : (v << 16));
 }
 
@@ -115,7 +117,7 @@ __device__ __forceinline__ float stored_target(const uint8_t *Yt, int L, int tgt
 // over the observation window of every E, times (E-1)tau+Tp .. L-1.  The
 // windows are nested, so one pass over the longest suffix plus the pieces
 // between consecutive starts gives all of them.
-template <bool BF16>
+template <bool BF16, int RW>
 __global__ void target_sums_kernel(const uint8_t *__restrict__ Yt, int N, int L, int tau, int Tp,
                                    double *__restrict__ ysum, double *__restrict__ yysum) {
     const int tgt = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = lane_id();
@@ -125,7 +127,7 @@ __global__ void target_sums_kernel(const uint8_t *__restrict__ Yt, int N, int L,
     const int start_top = (e_top - 1) * tau + Tp;
     double s1 = 0.0, s2 = 0.0;
     for (int u = start_top + lane; u < L; u += 32) {
-        const double v = stored_target<BF16>(Yt, L, tgt, u);
+        const double v = stored_target<BF16, RW>(Yt, L, tgt, u);
         s1 += v;
         s2 += v * v;
     }
@@ -137,7 +139,7 @@ __global__ void target_sums_kernel(const uint8_t *__restrict__ Yt, int N, int L,
         if (E < e_top) {
             // add times start .. start(E+1)-1
             for (int u = start; u < E * tau + Tp && u < L; ++u) {
-                const double v = stored_target<BF16>(Yt, L, tgt, u);
+                const double v = stored_target<BF16, RW>(Yt, L, tgt, u);
                 s1 += v;
                 s2 += v * v;
             }
@@ -148,37 +150,63 @@ __global__ void target_sums_kernel(const uint8_t *__restrict__ Yt, int N, int L,
     }
 }
 
-static int targets_per_tile(edm_precision prec) { return prec == EDM_BF16_TARGETS ? 64 : 32; }
+// Shared memory a lookup CTA needs besides its tile: the hand-over buffer,
+// at least two 4 KB table stages and the mbarriers.
+static size_t lookup_fixed_bytes(edm_precision prec) {
+    const size_t red = sizeof(float) * (prec == EDM_BF16_TARGETS ? LkCfg<true>::RED_FLOATS
+                                                                  : LkCfg<false>::RED_FLOATS);
+    return red + (2 * LK_MAX_STAGES + 4) * sizeof(uint64_t);
+}
 
-size_t target_store_bytes(int N_tgt, int L, edm_precision prec) {
-    const int tt = targets_per_tile(prec);
+int lookup_row_words(edm_ctx *ctx, int L, edm_precision prec) {
+    const size_t limit = static_cast<size_t>(ctx->max_smem_optin);
+    const size_t need = lookup_fixed_bytes(prec) + 2 * 4096;
+    if (static_cast<size_t>(L + 1) * 128 + need <= limit) return 32;
+    if (static_cast<size_t>(L + 1) * 64 + need <= limit) return 16;
+    return 32;  // the tile stays in global memory
+}
+
+static int targets_per_tile(edm_precision prec, int rw) {
+    return prec == EDM_BF16_TARGETS ? 2 * rw : rw;
+}
+
+size_t target_store_bytes(int N_tgt, int L, edm_precision prec, int rw) {
+    const int tt = targets_per_tile(prec, rw);
     const size_t tiles = (N_tgt + tt - 1) / tt;
-    return align_up(tiles * (L + 1) * LK_TILE_ROW, 256);
+    return align_up(tiles * (L + 1) * 4 * rw, 256);
 }
 
 edm_status launch_target_store(edm_ctx *ctx, const float *Y, long long ld, const int32_t *rows,
-                               int N_tgt, int L, int tau, int Tp, edm_precision prec, uint8_t *Yt,
-                               double *mean_ws, double *ysum, double *yysum) {
+                               int N_tgt, int L, int tau, int Tp, edm_precision prec, int rw,
+                               uint8_t *Yt, double *mean_ws, double *ysum, double *yysum) {
     const int warps_blocks = (N_tgt * 32 + 255) / 256;
     before_launch(ctx);
     target_mean_kernel<<<warps_blocks, 256, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean_ws);
     edm_status st = after_launch(ctx, "target_mean_kernel");
     if (st != EDM_OK) return st;
-    const int tt = targets_per_tile(prec);
+    const int tt = targets_per_tile(prec, rw);
     dim3 grid((N_tgt + tt - 1) / tt, (L + 31) / 32), block(32, 8);
     const bool bf16 = prec == EDM_BF16_TARGETS;
     before_launch(ctx);
-    if (bf16)
-        target_store_kernel<true><<<grid, block, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean_ws, Yt);
+    if (bf16 && rw == 16)
+        target_store_kernel<true, 16><<<grid, block, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean_ws, Yt);
+    else if (bf16)
+        target_store_kernel<true, 32><<<grid, block, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean_ws, Yt);
+    else if (rw == 16)
+        target_store_kernel<false, 16><<<grid, block, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean_ws, Yt);
     else
-        target_store_kernel<false><<<grid, block, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean_ws, Yt);
+        target_store_kernel<false, 32><<<grid, block, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean_ws, Yt);
     st = after_launch(ctx, "target_store_kernel");
     if (st != EDM_OK) return st;
     before_launch(ctx);
-    if (bf16)
-        target_sums_kernel<true><<<warps_blocks, 256, 0, ctx->stream>>>(Yt, N_tgt, L, tau, Tp, ysum, yysum);
+    if (bf16 && rw == 16)
+        target_sums_kernel<true, 16><<<warps_blocks, 256, 0, ctx->stream>>>(Yt, N_tgt, L, tau, Tp, ysum, yysum);
+    else if (bf16)
+        target_sums_kernel<true, 32><<<warps_blocks, 256, 0, ctx->stream>>>(Yt, N_tgt, L, tau, Tp, ysum, yysum);
+    else if (rw == 16)
+        target_sums_kernel<false, 16><<<warps_blocks, 256, 0, ctx->stream>>>(Yt, N_tgt, L, tau, Tp, ysum, yysum);
     else
-        target_sums_kernel<false><<<warps_blocks, 256, 0, ctx->stream>>>(Yt, N_tgt, L, tau, Tp, ysum, yysum);
+        target_sums_kernel<false, 32><<<warps_blocks, 256, 0, ctx->stream>>>(Yt, N_tgt, L, tau, Tp, ysum, yysum);
     return after_launch(ctx, "target_sums_kernel");
 }
 
@@ -267,11 +295,55 @@ __device__ __forceinline__ void lookup_pair(const uint8_t *blk, const uint32_t *
     }
 }
 
+// Half-row layout (16-word tile rows): half-warp h = lane/16 takes row 2p+h
+// of the pair block and lane l its tile word l%16, so one gather reads two
+// rows of 16 words.  Same prediction formula as lookup_pair; the moments
+// go to the .x lanes of the pair accumulators.
+template <int K, bool BF16>
+__device__ __forceinline__ void lookup_pair_half(const uint8_t *blk, const uint32_t *tl, int h,
+                                                 uint32_t yv, PairMoments<BF16> &m) {
+    constexpr int PB = table_pair_bytes(K);
+    constexpr int NV = PB / 16;
+    uint32_t wd[4 * NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        const uint4 v = reinterpret_cast<const uint4 *>(blk)[q];
+        wd[4 * q + 0] = v.x;
+        wd[4 * q + 1] = v.y;
+        wd[4 * q + 2] = v.z;
+        wd[4 * q + 3] = v.w;
+    }
+    uint32_t g[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        const int iw = 2 * (K - 1 + (q >> 1));
+        const uint32_t hw = h ? wd[iw + 1] : wd[iw];
+        const uint32_t u = (q & 1) ? (hw >> 16) : (hw & 0xffffu);
+        g[q] = tl[u * 16];
+    }
+#pragma unroll
+    for (int c = 0; c < PairMoments<BF16>::T; ++c) {
+        auto val = [&](uint32_t v) {
+            return __uint_as_float(BF16 ? (c == 0 ? (v << 16) : (v & 0xffff0000u)) : v);
+        };
+        const float yl = val(g[K - 1]);
+        float acc = yl;
+#pragma unroll
+        for (int q = 0; q < K - 1; ++q) {
+            const float w = __uint_as_float(h ? wd[2 * q + 1] : wd[2 * q]);
+            acc = __fmaf_rn(w, __fmaf_rn(yl, -1.f, val(g[q])), acc);
+        }
+        m.s[c].x = __fadd_rn(m.s[c].x, acc);
+        m.ss[c].x = __fmaf_rn(acc, acc, m.ss[c].x);
+        m.sy[c].x = __fmaf_rn(acc, val(yv), m.sy[c].x);
+    }
+}
+
 // Gather + accumulate one group whose k = K is a compile-time value: warps
 // take pairs warp, warp + NC, ... of each stage; a pair's observations are
 // read once and serve every member of the group.  All G slots are processed
 // (the empty slots of a partial group hold a copy of its first member).
-template <int K, bool BF16, bool SMEM_TILE>
+template <int K, bool BF16, bool SMEM_TILE, bool HALF>
 __device__ __forceinline__ void consume_group(const LookupArgs &a, const uint8_t *tile,
                                               const uint8_t *stages, uint64_t *full,
                                               uint64_t *empty, int &seq, int n, int t0,
@@ -281,8 +353,30 @@ __device__ __forceinline__ void consume_group(const LookupArgs &a, const uint8_t
     constexpr int GPB = C::G * PB;
     const int CP = a.stage_bytes / GPB;
     const int warp = threadIdx.x >> 5, lane = lane_id();
-    const uint32_t *tl = reinterpret_cast<const uint32_t *>(tile) + lane;
+    const uint32_t *tl = reinterpret_cast<const uint32_t *>(tile) + (HALF ? (lane & 15) : lane);
+    const int h = lane >> 4;
     const int npairs = (n + 1) >> 1;
+    if (HALF) {
+        for (int p0 = 0; p0 < npairs; p0 += CP) {
+            const int s = seq % a.stages;
+            const uint32_t par = (seq / a.stages) & 1;
+            mbar_wait_bounded(&full[s], par, a.flags);
+            const uint8_t *st = stages + static_cast<size_t>(s) * a.stage_bytes;
+            const int pairs = min(CP, npairs - p0);
+            const int ybase = t0 + a.Tp + 2 * p0 + h;
+            for (int p = warp; p < pairs; p += C::NC) {
+                const uint32_t yv = tl[(ybase + 2 * p) * 16];
+                const uint8_t *blk = st + static_cast<size_t>(p) * GPB;
+#pragma unroll
+                for (int m = 0; m < C::G; ++m)
+                    lookup_pair_half<K, BF16>(blk + m * PB, tl, h, yv, pm[m]);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            ++seq;
+        }
+        return;
+    }
     for (int p0 = 0; p0 < npairs; p0 += CP) {
         const int s = seq % a.stages;
         const uint32_t par = (seq / a.stages) & 1;
@@ -312,17 +406,20 @@ __device__ __forceinline__ float finish_rho(double n, double sa, double saa, dou
     return static_cast<float>(pearson_from_moments(n, sa, sb, saa, sbb, sab));
 }
 
-template <bool BF16, bool SMEM_TILE>
+// HALF: 16-word tile rows (see lookup_pair_half); only with the tile in
+// shared memory.
+template <bool BF16, bool SMEM_TILE, bool HALF>
 __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const LookupArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     using C = LkCfg<BF16>;
-    constexpr int TT = BF16 ? 64 : 32;
+    constexpr int RW = HALF ? 16 : 32;            // words per tile row
+    constexpr int TT = BF16 ? 2 * RW : RW;        // targets per tile
     constexpr int G = C::G, NM = C::NM;
     const int g0 = blockIdx.y * a.GB;
     const int g1 = min(*a.grp.count, g0 + a.GB);
     if (g0 >= g1) return;  // every thread of the CTA leaves here together
     const int tile_id = blockIdx.x;
-    const size_t tile_bytes = static_cast<size_t>(a.L + 1) * LK_TILE_ROW;
+    const size_t tile_bytes = static_cast<size_t>(a.L + 1) * 4 * RW;
     const uint8_t *tile_g = a.Yt + static_cast<size_t>(tile_id) * tile_bytes;
     uint8_t *tile_s = smem;
     uint8_t *stages = smem + (SMEM_TILE ? tile_bytes : 0);
@@ -415,13 +512,14 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
             for (int m = 0; m < G; ++m) {
                 if (m >= nm) continue;
                 float *rho_row = a.rho + static_cast<long long>(libs[m] - a.lib0) * a.rho_ld;
+                if (HALF && lane >= 16) continue;
                 if (!BF16) {
-                    const int tgt = tile_id * 32 + lane;
+                    const int tgt = tile_id * TT + lane;
                     if (tgt < a.N_tgt)
                         rho_row[rho_column(a, tgt)] = finish_rho(dn, S[m][0], S[m][1], S[m][2],
                                                                  a.ysum[wo + tgt], a.yysum[wo + tgt]);
                 } else {
-                    const int tgt = tile_id * 64 + 2 * lane;
+                    const int tgt = tile_id * TT + 2 * lane;
                     if (tgt < a.N_tgt)
                         rho_row[rho_column(a, tgt)] = finish_rho(dn, S[m][0], S[m][1], S[m][2],
                                                                  a.ysum[wo + tgt], a.yysum[wo + tgt]);
@@ -453,7 +551,7 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
                 pm[m].s[c] = pm[m].ss[c] = pm[m].sy[c] = f2(0.f, 0.f);
         switch (E + 1) {
 #define EDM_CASE(k) \
-    case k: consume_group<k, BF16, SMEM_TILE>(a, tile, stages, full, empty, seq, n, t0, pm); break;
+    case k: consume_group<k, BF16, SMEM_TILE, HALF>(a, tile, stages, full, empty, seq, n, t0, pm); break;
             EDM_CASE(2) EDM_CASE(3) EDM_CASE(4) EDM_CASE(5) EDM_CASE(6) EDM_CASE(7) EDM_CASE(8)
             EDM_CASE(9) EDM_CASE(10) EDM_CASE(11) EDM_CASE(12) EDM_CASE(13) EDM_CASE(14)
             EDM_CASE(15) EDM_CASE(16) EDM_CASE(17) EDM_CASE(18) EDM_CASE(19) EDM_CASE(20)
@@ -478,9 +576,18 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
             float *rb = rb0 + m * NM * 32;
 #pragma unroll
             for (int c = 0; c < PairMoments<BF16>::T; ++c) {
-                float v0 = pm[m].s[c].x + pm[m].s[c].y;
-                float v1 = pm[m].ss[c].x + pm[m].ss[c].y;
-                float v2 = pm[m].sy[c].x + pm[m].sy[c].y;
+                // row pairs: the two rows of a lane (FFMA2 lanes), or the
+                // two half-warps (HALF)
+                float v0, v1, v2;
+                if (HALF) {
+                    v0 = pm[m].s[c].x + __shfl_xor_sync(FULL, pm[m].s[c].x, 16);
+                    v1 = pm[m].ss[c].x + __shfl_xor_sync(FULL, pm[m].ss[c].x, 16);
+                    v2 = pm[m].sy[c].x + __shfl_xor_sync(FULL, pm[m].sy[c].x, 16);
+                } else {
+                    v0 = pm[m].s[c].x + pm[m].s[c].y;
+                    v1 = pm[m].ss[c].x + pm[m].ss[c].y;
+                    v2 = pm[m].sy[c].x + pm[m].sy[c].y;
+                }
                 if (!upper) {
                     v0 += rb[(3 * c + 0) * 32 + lane];
                     v1 += rb[(3 * c + 1) * 32 + lane];
@@ -512,7 +619,7 @@ static int ceil_log2(long long v) {
 }
 
 uint64_t lookup_bucket(int L, int N_tgt, int nlib, edm_precision prec) {
-    const int tt = targets_per_tile(prec);
+    const int tt = targets_per_tile(prec, 32);
     const int n_tiles = (N_tgt + tt - 1) / tt;
     return (static_cast<uint64_t>(ceil_log2(L)) << 24) | (static_cast<uint64_t>(ceil_log2(n_tiles)) << 16) |
            (static_cast<uint64_t>(ceil_log2(nlib)) << 8) | static_cast<uint64_t>(prec);
@@ -520,22 +627,24 @@ uint64_t lookup_bucket(int L, int N_tgt, int nlib, edm_precision prec) {
 
 edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, const uint8_t *tables,
                          const CcmGroups &g, int lib0, int nlib, int tau, int Tp,
-                         edm_precision prec, const double *ysum, const double *yysum, float *rho,
-                         long long rho_ld, const int32_t *rho_col) {
+                         edm_precision prec, int rw, const double *ysum, const double *yysum,
+                         float *rho, long long rho_ld, const int32_t *rho_col) {
     const bool bf16 = prec == EDM_BF16_TARGETS;
-    const int tt = targets_per_tile(prec);
+    const bool half = rw == 16;
+    const int tt = targets_per_tile(prec, rw);
     const int n_tiles = (N_tgt + tt - 1) / tt;
     const int threads = bf16 ? LkCfg<true>::THREADS : LkCfg<false>::THREADS;
     const int G = bf16 ? LkCfg<true>::G : LkCfg<false>::G;
     if (g.G != G) return set_error(ctx, EDM_ERR_INTERNAL, "lookup: group size mismatch");
     const size_t red_bytes =
         sizeof(float) * (bf16 ? LkCfg<true>::RED_FLOATS : LkCfg<false>::RED_FLOATS);
-    const size_t tile_bytes = static_cast<size_t>(L + 1) * LK_TILE_ROW;
+    const size_t tile_bytes = static_cast<size_t>(L + 1) * 4 * rw;
     const size_t fixed = red_bytes + (2 * LK_MAX_STAGES + 4) * sizeof(uint64_t);
     const size_t limit = static_cast<size_t>(ctx->max_smem_optin);
     // stages of 6 KB (4 KB when the tile leaves less room); at least two
     const size_t min_stage = 4096, big_stage = 6144;
     const bool smem_tile = tile_bytes + fixed + 2 * min_stage <= limit && tile_bytes < (1u << 20);
+    if (half && !smem_tile) return set_error(ctx, EDM_ERR_INTERNAL, "lookup: half tile does not fit");
     const size_t avail = limit - fixed - (smem_tile ? tile_bytes : 0);
     const size_t stage_bytes = avail >= 2 * big_stage ? big_stage : min_stage;
     const int stages = static_cast<int>(std::min<size_t>(LK_MAX_STAGES, avail / stage_bytes));
@@ -573,10 +682,12 @@ edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, cons
     a.flags = ctx->d_flags;
     dim3 grid(n_tiles, static_cast<unsigned>((g.ngroups_max + GB - 1) / GB));
     void (*kern)(const LookupArgs);
-    if (bf16)
-        kern = smem_tile ? lookup_kernel<true, true> : lookup_kernel<true, false>;
+    if (half)
+        kern = bf16 ? lookup_kernel<true, true, true> : lookup_kernel<false, true, true>;
+    else if (bf16)
+        kern = smem_tile ? lookup_kernel<true, true, false> : lookup_kernel<true, false, false>;
     else
-        kern = smem_tile ? lookup_kernel<false, true> : lookup_kernel<false, false>;
+        kern = smem_tile ? lookup_kernel<false, true, false> : lookup_kernel<false, false, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     before_launch(ctx);
     kern<<<grid, threads, smem, ctx->stream>>>(a);

@@ -89,12 +89,22 @@ def test_mixed_E_in_one_launch():
     check_ccm(X, X, E_lib, 1, 0, "fp32", TOL_FP32)
 
 
+@pytest.mark.parametrize("L,N", [(1700, 37), (2500, 40), (3250, 21)])
+def test_half_width_target_tiles(L, N):
+    # 1,600 < L <= 3,300: a 32-word tile row no longer fits shared memory, a
+    # 16-word one does (two half-warps take the two rows of a pair)
+    X = inputs.coupled_logistic(N, L, 12 + L)
+    E_lib = np.array([1, 2, 3, 4, 7] * 8, np.int32)[:N]
+    check_ccm(X, X, E_lib, 1, 0, "fp32", TOL_FP32, lib_rows=[0, 13, N - 1])
+    check_ccm(X, X, E_lib, 1, 0, "bf16", TOL_BF16, lib_rows=[0, 13, N - 1])
+
+
 def test_long_series_gathers_from_global_memory():
-    # L = 2500: a 32-target FP32 tile no longer fits shared memory
-    X = inputs.coupled_logistic(40, 2500, 12)
-    E_lib = np.array([1, 2, 3, 4] * 10, np.int32)
-    check_ccm(X, X, E_lib, 1, 0, "fp32", TOL_FP32, lib_rows=[0, 13, 39])
-    check_ccm(X, X, E_lib, 1, 0, "bf16", TOL_BF16, lib_rows=[0, 13, 39])
+    # L = 3,600: not even a 16-word tile fits; gathers read global memory
+    X = inputs.coupled_logistic(35, 3600, 13)
+    E_lib = np.array([1, 2, 3, 4, 5] * 7, np.int32)
+    check_ccm(X, X, E_lib, 1, 0, "fp32", TOL_FP32, lib_rows=[0, 13, 34])
+    check_ccm(X, X, E_lib, 1, 0, "bf16", TOL_BF16, lib_rows=[0, 13, 34])
 
 
 def test_self_map_equals_simplex():
