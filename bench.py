@@ -301,9 +301,10 @@ def run_gb300(args):
         steps_e2e = max(1, min(args.steps, 2))
 
         def e2e_step():
+            # series up; rho streamed down block by block as it is finished
             Xg.copy_(X_h, non_blocking=True)
-            step(args.precision)
-            rho_h.copy_(rho, non_blocking=True)
+            E_opt, _ = edm.edm_simplex_optimal_E(Xg, E_MAX, TAU, TP_SEL, with_rho=False)
+            edm.edm_ccm_all_host(Xg, Xg, E_opt, rho, rho_h, TAU, TP, args.precision)
 
         e2e_step()
         torch.cuda.synchronize(dev)

@@ -188,6 +188,20 @@ edm_status edm_ccm_all(edm_ctx *ctx, const float *X_lib, int N_lib,
                        const int32_t *E_lib, int tau, int Tp,
                        edm_precision prec, float *rho);
 
+/* edm_ccm_all that also delivers rho to host memory (no counterpart in the
+ * paper).  rho [N_lib][N_tgt] (device) as in edm_ccm_all; rho_host: a
+ * page-locked host buffer of the same shape (cudaMallocHost or
+ * cudaHostRegister; other memory returns EDM_ERR_INVALID_ARG).  Library rows
+ * are computed in about 16 blocks; each finished block is copied to rho_host
+ * on a second stream while the next block computes, so only the last
+ * block's copy is not hidden.  Everything, copies included, is complete
+ * when work queued afterwards on the context's stream runs (edm_ctx_sync
+ * waits for it). */
+edm_status edm_ccm_all_host(edm_ctx *ctx, const float *X_lib, int N_lib,
+                            const float *Y_tgt, int N_tgt, int L,
+                            const int32_t *E_lib, int tau, int Tp,
+                            edm_precision prec, float *rho, float *rho_host);
+
 /* Pairwise CCM with the embedding dimension chosen per TARGET (section 3.3:
  * targets are grouped by their optimal E, and for each group every library
  * is embedded at that E and gets one neighbour table).  Arguments as for

@@ -126,11 +126,15 @@ static size_t ccm_workspace_bytes(edm_ctx *ctx, int N_lib, int N_tgt, int L, int
 // The N_tgt stored targets are Y rows tgt_rows[r] (rows 0.. when NULL); rho
 // rows are rho_ld apart and stored target r goes to column rho_cols[r]
 // (column r when NULL).
+// rho_host (optional, page-locked, rows rho_ld apart like rho): each block of
+// finished rows is copied there on the context's copy stream while the next
+// block computes; blocks are then at most max_block libraries.
 static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, int N_lib,
                           const float *Y_tgt, long long ld_tgt, int N_tgt, int L,
                           const int32_t *E_lib, int E_uniform, int tau, int Tp, edm_precision prec,
                           float *rho, long long rho_ld, const int32_t *tgt_rows,
-                          const int32_t *rho_cols) {
+                          const int32_t *rho_cols, float *rho_host = nullptr,
+                          int max_block = 0) {
     const int rw = lookup_row_words(ctx, L, prec);
     const size_t yt_bytes = target_store_bytes(N_tgt, L, prec, rw);
     const size_t mean_bytes = align_up(sizeof(double) * N_tgt, 256);
@@ -151,8 +155,10 @@ static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, in
     st = launch_target_store(ctx, Y_tgt, ld_tgt, tgt_rows, N_tgt, L, tau, Tp, prec, rw, Yt, mean,
                              ysum, yysum);
     if (st != EDM_OK) return st;
-    for (int c0 = 0; c0 < N_lib; c0 += chunk) {
-        const int nlib = std::min(chunk, N_lib - c0);
+    const int block = max_block > 0 ? std::min(chunk, max_block) : chunk;
+    int nblk = 0;
+    for (int c0 = 0; c0 < N_lib; c0 += block) {
+        const int nlib = std::min(block, N_lib - c0);
         const CcmGroups grp = carve_groups(gmem, nlib, G);
         st = launch_group_libs(ctx, E_lib, E_uniform, c0, nlib, L, tau, Tp, grp);
         if (st != EDM_OK) return st;
@@ -160,6 +166,34 @@ static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, in
         if (st != EDM_OK) return st;
         st = launch_lookup(ctx, Yt, N_tgt, L, tables, grp, c0, nlib, tau, Tp, prec, rw, ysum,
                            yysum, rho + static_cast<size_t>(c0) * rho_ld, rho_ld, rho_cols);
+        if (st != EDM_OK) return st;
+        if (rho_host) {
+            // copy this block's rows while the next block computes
+            if (static_cast<int>(ctx->copy_ev.size()) <= nblk) {
+                cudaEvent_t e = nullptr;
+                st = cuda_check(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming),
+                                "copy event");
+                if (st != EDM_OK) return st;
+                ctx->copy_ev.push_back(e);
+            }
+            cudaEvent_t ev = ctx->copy_ev[nblk++];
+            const size_t off = static_cast<size_t>(c0) * rho_ld;
+            st = cuda_check(ctx, cudaEventRecord(ev, ctx->stream), "copy order");
+            if (st == EDM_OK)
+                st = cuda_check(ctx, cudaStreamWaitEvent(ctx->copy_stream, ev, 0), "copy order");
+            if (st == EDM_OK)
+                st = cuda_check(ctx, cudaMemcpyAsync(rho_host + off, rho + off,
+                                                     sizeof(float) * nlib * rho_ld,
+                                                     cudaMemcpyDeviceToHost, ctx->copy_stream),
+                                "rho copy");
+            if (st != EDM_OK) return st;
+        }
+    }
+    if (rho_host && nblk > 0) {
+        // the context's stream (and a sync on it) waits for the copies
+        cudaEvent_t done = ctx->copy_ev[0];
+        st = cuda_check(ctx, cudaEventRecord(done, ctx->copy_stream), "copy done");
+        if (st == EDM_OK) st = cuda_check(ctx, cudaStreamWaitEvent(ctx->stream, done, 0), "copy done");
         if (st != EDM_OK) return st;
     }
     return EDM_OK;
@@ -415,6 +449,11 @@ edm_status edm_destroy(edm_ctx *ctx) {
     if (ctx->ev_done) cudaEventDestroy(ctx->ev_done);
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
     if (ctx->origin) cudaStreamDestroy(ctx->origin);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
+    for (cudaEvent_t e : ctx->copy_ev) cudaEventDestroy(e);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->d_flags) cudaFree(ctx->d_flags);
     prof_clear(ctx);
@@ -545,6 +584,31 @@ edm_status edm_ccm_all(edm_ctx *ctx, const float *X_lib, int N_lib, const float 
     DeviceGuard g(ctx->device);
     return ccm_one(ctx, X_lib, L, N_lib, Y_tgt, L, N_tgt, L, E_lib, 0, tau, Tp, prec, rho, N_tgt,
                    nullptr, nullptr);
+}
+
+edm_status edm_ccm_all_host(edm_ctx *ctx, const float *X_lib, int N_lib, const float *Y_tgt,
+                            int N_tgt, int L, const int32_t *E_lib, int tau, int Tp,
+                            edm_precision prec, float *rho, float *rho_host) {
+    if (!ctx) return EDM_ERR_INVALID_ARG;
+    if (!X_lib || !Y_tgt || !E_lib || !rho || !rho_host || N_lib < 1 || N_tgt < 1 ||
+        !series_len_ok(L) || tau < 1 || Tp < 0 || L - Tp < 3 ||
+        (prec != EDM_FP32 && prec != EDM_BF16_TARGETS))
+        return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_all_host: bad arguments");
+    DeviceGuard g(ctx->device);
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, rho_host) != cudaSuccess ||
+        attr.type != cudaMemoryTypeHost) {
+        cudaGetLastError();
+        return set_error(ctx, EDM_ERR_INVALID_ARG,
+                         "edm_ccm_all_host: rho_host must be page-locked host memory");
+    }
+    if (!ctx->copy_stream &&
+        cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return set_error(ctx, EDM_ERR_CUDA, "copy stream creation failed");
+    // about 16 blocks, so that only the last block's copy is left exposed
+    const int block = std::max(64, (N_lib + 15) / 16);
+    return ccm_one(ctx, X_lib, L, N_lib, Y_tgt, L, N_tgt, L, E_lib, 0, tau, Tp, prec, rho, N_tgt,
+                   nullptr, nullptr, rho_host, block);
 }
 
 edm_status edm_ccm_all_target_E(edm_ctx *ctx, const float *X_lib, int N_lib, const float *Y_tgt,

@@ -51,6 +51,10 @@ struct edm_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     uint64_t graph_key = 0;
     uint64_t graph_kernels = 0;  // kernels one replay of graph_exec launches
+
+    // copies of finished rho blocks to host memory (edm_ccm_all_host)
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> copy_ev;
 };
 
 // device-side error flags, OR-ed into ctx->d_flags

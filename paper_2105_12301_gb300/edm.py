@@ -79,6 +79,7 @@ def load():
     lib.edm_check_wait_timeout.argtypes = [vp, ci]
     lib.edm_predict.argtypes = [vp, vp, ci, vp, ci, ci, vp, vp, ci, ci, vp]
     lib.edm_ccm_all_target_E.argtypes = [vp, vp, ci, vp, ci, ci, vp, ci, ci, ci, vp]
+    lib.edm_ccm_all_host.argtypes = [vp, vp, ci, vp, ci, ci, vp, ci, ci, ci, vp, vp]
     lib.edm_profile_enable.argtypes = [vp, ci]
     lib.edm_profile_read.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ci)]
@@ -89,7 +90,7 @@ def load():
               "edm_profile_enable", "edm_profile_read", "edm_probe_smem_bandwidth",
               "edm_simplex_optimal_E_noalloc", "edm_ccm_window",
               "edm_simplex_optimal_E_batched", "edm_set_option", "edm_check_wait_timeout",
-              "edm_predict", "edm_ccm_all_target_E"):
+              "edm_predict", "edm_ccm_all_target_E", "edm_ccm_all_host"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -265,6 +266,33 @@ def edm_ccm_all(X_lib, Y_tgt, E_lib, tau=1, Tp=0, precision="fp32", out=None):
     _check(ctx, load().edm_ccm_all(ctx, _ptr(X_lib), N_lib, _ptr(Y_tgt), N_tgt, L, _ptr(E_lib),
                                    tau, Tp, _prec(precision), _ptr(rho)), "edm_ccm_all")
     return rho
+
+
+def edm_ccm_all_host(X_lib, Y_tgt, E_lib, out, out_host, tau=1, Tp=0, precision="fp32"):
+    """edm_ccm_all into the device tensor `out` [N_lib][N_tgt] and, block by
+    block while the computation continues, into the pinned CPU tensor
+    `out_host` of the same shape; both are complete once torch's current
+    stream reaches this point."""
+    _series(X_lib, "X_lib", 2)
+    _series(Y_tgt, "Y_tgt", 2)
+    if X_lib.shape[1] != Y_tgt.shape[1]:
+        raise ValueError("libraries and targets must have the same length")
+    N_lib, L = X_lib.shape
+    N_tgt = Y_tgt.shape[0]
+    if E_lib.dtype != torch.int32 or not E_lib.is_cuda or E_lib.shape != (N_lib,):
+        raise TypeError("E_lib must be a CUDA int32 tensor of shape [N_lib]")
+    for name, t, cuda in (("out", out, True), ("out_host", out_host, False)):
+        if (t.shape != (N_lib, N_tgt) or t.dtype != torch.float32 or not t.is_contiguous()
+                or t.is_cuda != cuda):
+            raise TypeError("%s must be a contiguous float32 [N_lib][N_tgt] %s tensor"
+                            % (name, "CUDA" if cuda else "CPU"))
+    if not out_host.is_pinned():
+        raise TypeError("out_host must be in pinned memory")
+    ctx = _ctx(X_lib.device)
+    _check(ctx, load().edm_ccm_all_host(ctx, _ptr(X_lib), N_lib, _ptr(Y_tgt), N_tgt, L,
+                                        _ptr(E_lib.contiguous()), tau, Tp, _prec(precision),
+                                        _ptr(out), _ptr(out_host)), "edm_ccm_all_host")
+    return out, out_host
 
 
 def edm_ccm_all_target_E(X_lib, Y_tgt, E_tgt, tau=1, Tp=0, precision="fp32", out=None):

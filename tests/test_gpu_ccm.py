@@ -265,3 +265,25 @@ def test_per_target_E_rule_matches_oracle():
     torch.testing.assert_close(a, b, rtol=0, atol=0)
     with pytest.raises(edm.EdmError):
         edm.edm_ccm_all_target_E(gpu(X), gpu(Y), gpu(np.full(Y.shape[0], 21, np.int32)))
+
+
+def test_ccm_all_host_streams_rows_to_pinned_memory():
+    X = inputs.config2(N=300, L=400)
+    E = check_optimal_E(X[:20], 8)
+    E_lib = np.resize(E, 300).astype(np.int32)
+    Xg = gpu(X)
+    out = torch.empty((300, 300), dtype=torch.float32, device="cuda")
+    host = torch.empty((300, 300), dtype=torch.float32).pin_memory()
+    edm.edm_ccm_all_host(Xg, Xg, gpu(E_lib), out, host, 1, 0, "fp32")
+    edm.edm_ctx_sync()
+    ref = edm.edm_ccm_all(Xg, Xg, gpu(E_lib), 1, 0, "fp32")
+    edm.edm_ctx_sync()
+    torch.testing.assert_close(out, ref, rtol=0, atol=0, equal_nan=True)
+    torch.testing.assert_close(host, ref.cpu(), rtol=0, atol=0, equal_nan=True)
+    with pytest.raises(edm.EdmError):   # pageable host memory is refused
+        edm.load()
+        ctx = edm._ctx(Xg.device)
+        st = edm.load().edm_ccm_all_host(ctx, edm._ptr(Xg), 300, edm._ptr(Xg), 300, 400,
+                                         edm._ptr(gpu(E_lib)), 1, 0, 0, edm._ptr(out),
+                                         edm._ptr(torch.empty((300, 300))))
+        edm._check(ctx, st, "edm_ccm_all_host")
