@@ -40,7 +40,8 @@ E_MAX, TAU, TP, TP_SEL = 20, 1, 0, 1
 
 # DRAM bytes per lookup_kernel launch from an ncu capture (profiles/), valid
 # only for the kernel source it was taken on.
-LOOKUP_TRAFFIC = {"source_sha1": None, "bytes_per_launch": None}
+LOOKUP_TRAFFIC = {"source_sha1": "e0ccb9b9ef11e9c353a852c602b4088a6a36d3c3",
+                  "bytes_per_launch": 26021198182}  # mean of the 5 launches of one step
 
 
 def workload(name):
@@ -452,14 +453,63 @@ def run_libsweep_workload(args):
     print(json.dumps(out), flush=True)
 
 
+def run_paper_micro_workload(args):
+    """The shapes of the paper's micro-benchmarks (section 4): exact all-kNN
+    of series of 10^4 steps for E = 1..20 (16 series, so the GPU is filled),
+    and the lookup of 10 libraries against 10^5 targets of 10^4 steps."""
+    from paper_2105_12301_gb300 import edm
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    L = 10000
+    X = inputs.config5(N=16, L=L)
+    Xg = torch.from_numpy(X).to(dev)
+    knn = {}
+    for E in range(1, E_MAX + 1):
+        def one():
+            edm.edm_knn(Xg, E, TAU, 0, with_dist=True)
+        one()
+        ms = sync_time(one, dev, stream, 1)
+        rows = X.shape[0] * (L - (E - 1) * TAU)
+        knn[str(E)] = {"ms": ms, "rows_per_s": rows / (ms / 1e3)}
+        log("knn E=%d %.1f ms" % (E, ms))
+    Y = inputs.ar1_series(100000, L, 2105)
+    log("generated targets %s" % (Y.shape,))
+    Yg = torch.from_numpy(Y).to(dev)
+    del Y
+    E_lib = torch.full((X.shape[0],), 3, dtype=torch.int32, device=dev)
+    lib = Xg[:10].contiguous()
+    rho = torch.empty((10, Yg.shape[0]), dtype=torch.float32, device=dev)
+    lookup = {}
+    for prec in ("fp32", "bf16"):
+        def one():
+            edm.edm_ccm_all(lib, Yg, E_lib[:10].contiguous(), TAU, TP, prec, out=rho)
+        one()
+        edm.edm_profile_enable(True, dev)
+        ms = sync_time(one, dev, stream, 1)
+        split = {k: edm.edm_profile_read(k, dev)[0] for k in
+                 ("target_store_kernel", "ccm_table_kernel", "lookup_kernel")}
+        edm.edm_profile_enable(False, dev)
+        edm.edm_ctx_sync(dev)
+        lookup[prec] = {"ms": ms, "pairs_per_s": 10 * Yg.shape[0] / (ms / 1e3), "kernel_ms": split}
+        log("lookup %s %.1f ms %s" % (prec, ms, split))
+    out = {"metric": "kNN rows/s and CCM pairs/s at the paper's micro-benchmark shapes",
+           "unit": "rows/s, pairs/s", "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": "knn: 16 coupled-logistic series x 10,000 steps, E = 1..20, exact "
+                                  "order; lookup: 10 libraries (E = 3) x 100,000 AR(1) targets x "
+                                  "10,000 steps", "tau": TAU, "Tp": TP},
+           "knn": knn, "lookup": lookup}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--workload", choices=["calcium50k", "calcium2k", "batched", "libsweep"],
-                    default="calcium50k")
+    ap.add_argument("--workload", choices=["calcium50k", "calcium2k", "batched", "libsweep",
+                                           "paper-micro"], default="calcium50k")
     ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
     ap.add_argument("--no-mixed", dest="mixed", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
@@ -471,6 +521,8 @@ def main():
         run_batched_workload(args)
     elif args.workload == "libsweep":
         run_libsweep_workload(args)
+    elif args.workload == "paper-micro":
+        run_paper_micro_workload(args)
     else:
         run_gb300(args)
 

@@ -182,3 +182,19 @@ def logistic_pair(L, seed, r_x=3.8, r_y=3.5, b_xy=0.0, b_yx=0.1, burn=200):
         if t >= burn:
             out[:, t - burn] = (x, y)
     return znorm32(out)
+
+
+def ar1_series(N, L, seed, phi=0.9, sigma=1.0, burn=50):
+    """N independent AR(1) series x(t+1) = phi x(t) + sigma e(t), float32
+    [N][L], generated a time step at a time (cheap for very many series);
+    stands in for the 10^5 targets x 10^4 steps of the paper's lookup
+    micro-benchmark."""
+    rng = np.random.default_rng(seed)
+    out_t = np.empty((L, N), np.float32)  # time-major while generating
+    x = rng.standard_normal(N, dtype=np.float32)
+    phi32, sig32 = np.float32(phi), np.float32(sigma)
+    for t in range(burn + L):
+        x = phi32 * x + sig32 * rng.standard_normal(N, dtype=np.float32)
+        if t >= burn:
+            out_t[t - burn] = x
+    return np.ascontiguousarray(out_t.T)
