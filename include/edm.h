@@ -241,6 +241,16 @@ edm_status edm_ccm_window(edm_ctx *ctx, const float *X, int N, int ld, int offse
                           int L_win, const int32_t *E_lib, int tau, int Tp,
                           edm_precision prec, float *rho);
 
+/* Convergence over several library windows of the same length (random or
+ * chosen windows, e.g. to average the skill at each library length):
+ * edm_ccm_window for every window w = 0..n_windows-1 starting at offsets[w]
+ * (a HOST array, read before the call returns; 0 <= offsets[w] and
+ * offsets[w] + L_win <= ld).  rho [n_windows][N][N] float32 (device):
+ * block w is the rho matrix of window w. */
+edm_status edm_ccm_windows(edm_ctx *ctx, const float *X, int N, int ld, const int *offsets,
+                           int n_windows, int L_win, const int32_t *E_lib, int tau, int Tp,
+                           edm_precision prec, float *rho);
+
 /* One all-to-all CCM problem inside a batch: the series X [N][L] are both
  * the libraries and the targets; only the library rows lib_begin..lib_end-1
  * are computed (so a problem can be split or resumed by row block).

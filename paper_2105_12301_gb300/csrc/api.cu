@@ -706,6 +706,26 @@ edm_status edm_predict(edm_ctx *ctx, const float *X_lib, int N_lib, const float 
     return EDM_OK;
 }
 
+edm_status edm_ccm_windows(edm_ctx *ctx, const float *X, int N, int ld, const int *offsets,
+                           int n_windows, int L_win, const int32_t *E_lib, int tau, int Tp,
+                           edm_precision prec, float *rho) {
+    if (!ctx) return EDM_ERR_INVALID_ARG;
+    if (!X || !offsets || !E_lib || !rho || N < 1 || n_windows < 1 || !series_len_ok(L_win) ||
+        tau < 1 || Tp < 0 || L_win - Tp < 3 || (prec != EDM_FP32 && prec != EDM_BF16_TARGETS))
+        return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_windows: bad arguments");
+    for (int w = 0; w < n_windows; ++w)
+        if (offsets[w] < 0 || static_cast<long long>(offsets[w]) + L_win > ld)
+            return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_windows: window %d out of range", w);
+    DeviceGuard g(ctx->device);
+    for (int w = 0; w < n_windows; ++w) {
+        const float *base = X + offsets[w];
+        edm_status st = ccm_one(ctx, base, ld, N, base, ld, N, L_win, E_lib, 0, tau, Tp, prec,
+                                rho + static_cast<size_t>(w) * N * N, N, nullptr, nullptr);
+        if (st != EDM_OK) return st;
+    }
+    return EDM_OK;
+}
+
 static bool instance_ok(const edm_instance &p) {
     return p.X && p.E_lib && p.N >= 1 && series_len_ok(p.L) && p.tau >= 1 && p.Tp >= 0 &&
            p.L - p.Tp >= 3 && p.lib_begin >= 0 && p.lib_end <= p.N && p.lib_begin <= p.lib_end;

@@ -12,6 +12,15 @@ namespace edm {
 constexpr int KNN_WARPS = 8;
 constexpr int SERIES_SMEM_MAX = 96 * 1024;  // stage the series when it fits
 
+// Series longer than 2,048 points: candidates in chunks of 32 slots per lane
+// (1,024 candidates) held in registers, selected against a running list.
+constexpr int TL_CH = 32;
+
+struct TableLongScratch {
+    WarpScratch ws;
+    uint64_t list[32];  // the R smallest FP32 keys seen so far, ascending
+};
+
 // ------------------------------------------------------------------ embed
 
 __global__ void embed_kernel(const float *__restrict__ x, int L, int E, int tau,
@@ -88,6 +97,13 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
     }
 }
 
+// edm_knn for series longer than 2,048 points: chunked candidates held in
+// registers against a running list (knn_row_chunked, exact FP64 order).
+template <bool SMEM>
+__global__ void __launch_bounds__(KNN_WARPS * 32)
+    knn_out_long_kernel(const float *__restrict__ X, int L, int E, int tau, int Tp, int K, int RB,
+                        int32_t *__restrict__ idx, float *__restrict__ dist);
+
 template <int E>
 static edm_status launch_knn_E(edm_ctx *ctx, const float *X, int N, int L, int tau, int Tp, int K,
                                int32_t *idx, float *dist) {
@@ -112,6 +128,19 @@ static edm_status launch_knn_E(edm_ctx *ctx, const float *X, int N, int L, int t
 
 edm_status launch_knn(edm_ctx *ctx, const float *X, int N, int L, int E, int tau, int Tp, int k,
                       int32_t *idx, float *dist) {
+    if (L > 2048 && E >= 1 && E <= EDM_E_MAX) {
+        const int n = L - (E - 1) * tau - Tp;
+        const int RB = rows_per_cta(ctx, N, n);
+        dim3 grid(N, (n + RB - 1) / RB);
+        const bool smem_series = sizeof(float) * static_cast<size_t>(L) <= SERIES_SMEM_MAX;
+        const size_t smem = KNN_WARPS * sizeof(TableLongScratch) +
+                            (smem_series ? align_up(sizeof(float) * L, 16) : 0);
+        auto kern = smem_series ? knn_out_long_kernel<true> : knn_out_long_kernel<false>;
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        before_launch(ctx);
+        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, L, E, tau, Tp, k, RB, idx, dist);
+        return after_launch(ctx, "knn_out_kernel");
+    }
     switch (E) {
 #define EDM_CASE(e) \
     case e: return launch_knn_E<e>(ctx, X, N, L, tau, Tp, k, idx, dist);
@@ -227,27 +256,24 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
 
 // ------------------------------------------- tables of long series (> 2,048)
 
-constexpr int TL_CH = 32;  // candidate slots per lane per chunk (1,024 candidates)
-
-struct TableLongScratch {
-    WarpScratch ws;
-    uint64_t list[32];  // the R = k+1 smallest FP32 keys seen so far, ascending
-};
-
-// The k = E+1 nearest neighbours (exact FP64 set) of the query time t among
-// the times lo..hi, from chunks of 1,024 candidates whose FP32 squared
-// distances are accumulated in registers (lag order 0..E-1, one fma per lag,
-// the same operations as dist32).  Each chunk is selected against a running
-// list of the R smallest keys, as in the long optimal-E sweep; then the FP64
-// band check of knn_row's KNN_SET mode.  On return lane r < K holds the r-th
-// neighbour and its distance.
-__device__ void table_row_long(const float *xs, int L, int t, int lo, int hi, int E, int tau,
-                               TableLongScratch *sc, int &u_out, float &d_out) {
+// The K nearest neighbours of the query time t among the times lo..hi, from
+// chunks of 1,024 candidates whose FP32 squared distances are accumulated in
+// registers (lag order 0..E-1, one fma per lag, the same operations as
+// dist32).  Each chunk is selected against a running list of the R smallest
+// keys, as in the long optimal-E sweep; then the FP64 step of knn_row:
+//   KNN_SET (R = K+1): the exact FP64 neighbour set, FP32 order and
+//     distances unless the band had to be resolved;
+//   KNN_ORDERED (R = K+KNN_MARGIN): the exact FP64 order (s64, u), d the
+//     FP64 square root rounded to float.
+// On return lane r < K holds the r-th neighbour and its distance.
+template <int MODE>
+__device__ void knn_row_chunked(const float *xs, int L, int t, int lo, int hi, int E, int tau,
+                                int K, TableLongScratch *sc, int &u_out, float &d_out) {
     const int lane = lane_id();
     WarpScratch *ws = &sc->ws;
     uint64_t *list = sc->list;
-    const int K = E + 1;
-    const int R = min(K + 1, hi - lo);
+    const int nc = hi - lo;
+    const int R = MODE == KNN_ORDERED ? min(K + KNN_MARGIN, nc) : min(K + 1, nc);
     int have = 0;
     bool deg = false;
     for (int c0 = 0; c0 <= hi; c0 += 32 * TL_CH) {
@@ -318,10 +344,36 @@ __device__ void table_row_long(const float *xs, int L, int t, int lo, int hi, in
     }
     if (!deg) {
         const float edge = band_edge(key_s(list[K - 1]), E);
-        if (R <= K || key_s(list[K]) > edge) {
+        if (MODE == KNN_SET && (R <= K || key_s(list[K]) > edge)) {
             if (lane < K) {
                 u_out = key_u(list[lane]);
                 d_out = sqrtf(key_s(list[lane]));
+            }
+            __syncwarp();
+            return;
+        }
+        if (MODE == KNN_ORDERED && (R == nc || key_s(list[R - 1]) > edge)) {
+            // the R collected keys cover the band: rank them in FP64
+            double s64 = __longlong_as_double(0x7ff0000000000000LL);
+            int u = 0x7fffffff;
+            if (lane < R) {
+                u = key_u(list[lane]);
+                s64 = dist64(xs, t, u, E, tau);
+            }
+            int rank = 0;
+            for (int j = 0; j < R; ++j) {
+                const double sj = __shfl_sync(FULL, s64, j);
+                const int uj = __shfl_sync(FULL, u, j);
+                rank += less64(sj, uj, s64, u);
+            }
+            if (lane < R && rank < K) {
+                ws->sel_s64[rank] = s64;
+                ws->sel_u[rank] = u;
+            }
+            __syncwarp();
+            if (lane < K) {
+                u_out = ws->sel_u[lane];
+                d_out = __double2float_rn(__dsqrt_rn(ws->sel_s64[lane]));
             }
             __syncwarp();
             return;
@@ -377,9 +429,34 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
     for (int i = r0 + warp; i < r1; i += KNN_WARPS) {
         int u = 0;
         float d = 0.f;
-        table_row_long(xs, L, lo + i, lo, hi, E, tau, sc, u, d);
+        knn_row_chunked<KNN_SET>(xs, L, lo + i, lo, hi, E, tau, E + 1, sc, u, d);
         const float w = simplex_weight(d, E + 1);
         write_table_row(ts.base, ts.pair_stride, i, n, E + 1, L, Tp, u, w);
+    }
+}
+
+template <bool SMEM>
+__global__ void __launch_bounds__(KNN_WARPS * 32)
+    knn_out_long_kernel(const float *__restrict__ X, int L, int E, int tau, int Tp, int K, int RB,
+                        int32_t *__restrict__ idx, float *__restrict__ dist) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    TableLongScratch *sca = reinterpret_cast<TableLongScratch *>(smem);
+    float *xs_s = reinterpret_cast<float *>(smem + KNN_WARPS * sizeof(TableLongScratch));
+    const int series = blockIdx.x;
+    const float *xs = stage_series<SMEM>(X + static_cast<size_t>(series) * L, L, xs_s);
+    const int lo = (E - 1) * tau, hi = L - 1 - Tp, n = hi - lo + 1;
+    const int r0 = blockIdx.y * RB, r1 = min(n, r0 + RB);
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    TableLongScratch *sc = sca + warp;
+    for (int i = r0 + warp; i < r1; i += KNN_WARPS) {
+        int u = 0;
+        float d = 0.f;
+        knn_row_chunked<KNN_ORDERED>(xs, L, lo + i, lo, hi, E, tau, K, sc, u, d);
+        const size_t o = (static_cast<size_t>(series) * n + i) * K;
+        if (lane < K) {
+            idx[o + lane] = u;
+            if (dist) dist[o + lane] = d;
+        }
     }
 }
 

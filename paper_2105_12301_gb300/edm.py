@@ -80,6 +80,7 @@ def load():
     lib.edm_predict.argtypes = [vp, vp, ci, vp, ci, ci, vp, vp, ci, ci, vp]
     lib.edm_ccm_all_target_E.argtypes = [vp, vp, ci, vp, ci, ci, vp, ci, ci, ci, vp]
     lib.edm_ccm_all_host.argtypes = [vp, vp, ci, vp, ci, ci, vp, ci, ci, ci, vp, vp]
+    lib.edm_ccm_windows.argtypes = [vp, vp, ci, ci, ctypes.POINTER(ci), ci, ci, vp, ci, ci, ci, vp]
     lib.edm_profile_enable.argtypes = [vp, ci]
     lib.edm_profile_read.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ci)]
@@ -90,7 +91,7 @@ def load():
               "edm_profile_enable", "edm_profile_read", "edm_probe_smem_bandwidth",
               "edm_simplex_optimal_E_noalloc", "edm_ccm_window",
               "edm_simplex_optimal_E_batched", "edm_set_option", "edm_check_wait_timeout",
-              "edm_predict", "edm_ccm_all_target_E", "edm_ccm_all_host"):
+              "edm_predict", "edm_ccm_all_target_E", "edm_ccm_all_host", "edm_ccm_windows"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -351,6 +352,25 @@ def edm_ccm_window(X, offset, L_win, E_lib, tau=1, Tp=0, precision="fp32", out=N
     ctx = _ctx(X.device)
     _check(ctx, load().edm_ccm_window(ctx, _ptr(X), N, ld, offset, L_win, _ptr(E_lib.contiguous()),
                                       tau, Tp, _prec(precision), _ptr(rho)), "edm_ccm_window")
+    return rho
+
+
+def edm_ccm_windows(X, offsets, L_win, E_lib, tau=1, Tp=0, precision="fp32", out=None):
+    """rho [n_windows][N][N]: all-to-all CCM on the windows
+    X[:, o:o+L_win] for every offset o in `offsets` (a list of ints)."""
+    _series(X, "X", 2)
+    N, ld = X.shape
+    if E_lib.dtype != torch.int32 or not E_lib.is_cuda or E_lib.shape != (N,):
+        raise TypeError("E_lib must be a CUDA int32 tensor of shape [N]")
+    offs = (ctypes.c_int * len(offsets))(*[int(o) for o in offsets])
+    rho = out if out is not None else torch.empty((len(offsets), N, N), dtype=torch.float32,
+                                                  device=X.device)
+    if rho.shape != (len(offsets), N, N) or rho.dtype != torch.float32 or not rho.is_contiguous():
+        raise TypeError("out must be a contiguous float32 [n_windows][N][N] tensor")
+    ctx = _ctx(X.device)
+    _check(ctx, load().edm_ccm_windows(ctx, _ptr(X), N, ld, offs, len(offsets), L_win,
+                                       _ptr(E_lib.contiguous()), tau, Tp, _prec(precision),
+                                       _ptr(rho)), "edm_ccm_windows")
     return rho
 
 

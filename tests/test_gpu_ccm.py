@@ -287,3 +287,21 @@ def test_ccm_all_host_streams_rows_to_pinned_memory():
                                          edm._ptr(gpu(E_lib)), 1, 0, 0, edm._ptr(out),
                                          edm._ptr(torch.empty((300, 300))))
         edm._check(ctx, st, "edm_ccm_all_host")
+
+
+def test_random_library_windows_match_oracle():
+    # several windows of one length (e.g. random starts for convergence curves)
+    X = inputs.coupled_logistic(10, 900, 93)
+    E = np.array([2, 3, 1, 2, 4, 2, 3, 5, 2, 1], np.int32)
+    rng = np.random.default_rng(4)
+    L_win = 250
+    offs = sorted(rng.choice(900 - L_win + 1, 4, replace=False).tolist())
+    rho = edm.edm_ccm_windows(gpu(X), offs, L_win, gpu(E), 1, 0, "fp32")
+    edm.edm_ctx_sync()
+    rho = rho.cpu().numpy()
+    for w, o in enumerate(offs):
+        Xw = np.ascontiguousarray(X[:, o:o + L_win])
+        ref = oracle.ccm_matrix(Xw, Xw, E, 1, 0)
+        assert np.max(np.abs(rho[w] - ref)) <= TOL_FP32, (w, o)
+    with pytest.raises(edm.EdmError):
+        edm.edm_ccm_windows(gpu(X), [700], L_win, gpu(E))   # runs past the end

@@ -102,3 +102,18 @@ def test_knn_rejects_bad_arguments():
         edm.edm_knn(X, 2, 1, 0, k=25)     # k above EDM_K_MAX
     with pytest.raises(edm.EdmError):
         edm.edm_knn(gpu(np.zeros((1, 4), np.float32)), 2, 1, 0, k=3)  # too few points
+
+
+@pytest.mark.parametrize("E,tau,Tp,k", [(1, 1, 0, 2), (3, 2, 1, 4), (12, 1, 0, 13), (20, 1, 2, 24)])
+def test_knn_chunked_long_series_exact_order(E, tau, Tp, k):
+    # 2,048 < L: candidates in chunks of 1,024 against a running list; the
+    # exact FP64 order, also for k != E+1 and at the largest k
+    x = inputs.coupled_logistic(1, 5000, 300 + E)[0]
+    x[1000:1010] = x[2000:2010]                      # exact repeats: ties
+    idx, dist = edm.edm_knn(gpu(x[None]), E, tau, Tp, k=k)
+    idx, dist = idx[0].cpu().numpy(), dist[0].cpu().numpy()
+    lo = (E - 1) * tau
+    for t in (lo, lo + 1, 1005, 2005, 4000, 5000 - 1 - Tp):
+        oi, od = oracle.knn_row(x, E, tau, Tp, t, k=k)
+        np.testing.assert_array_equal(idx[t - lo], oi)
+        np.testing.assert_array_equal(dist[t - lo], od.astype(np.float32))
