@@ -151,7 +151,7 @@ def run_reference(args):
     if rank != 0:
         return
     N, L = workload(args.workload)
-    X = inputs.config3(N, L)
+    X = inputs.calcium(N, L)
     cores = os.cpu_count() or 1
     threads = cores
     n_libs = threads
@@ -195,7 +195,7 @@ def run_gb300(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     N, L = workload(args.workload)
-    X = inputs.config3(N, L, seed=ranks.problem_seed(1003, rank))
+    X = inputs.calcium(N, L, seed=ranks.problem_seed(1003, rank))
     Xg = torch.from_numpy(X).to(dev)
     rho = torch.empty((N, N), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -367,10 +367,10 @@ def run_batched_workload(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    Ns, Ls = inputs.config4_shapes()
+    Ns, Ls = inputs.uneven_batch_shapes()
     probs, E_out, pairs = [], [], 0.0
     for i, (N, L) in enumerate(zip(Ns, Ls)):
-        X = torch.from_numpy(inputs.config4_instance(i, N, L)).to(dev)
+        X = torch.from_numpy(inputs.uneven_batch_instance(i, N, L)).to(dev)
         E = torch.empty(int(N), dtype=torch.int32, device=dev)
         rho = torch.empty((int(N), int(N)), dtype=torch.float32, device=dev)
         probs.append({"X": X, "tau": TAU, "Tp": TP, "E_lib": E, "rho": rho})
@@ -419,7 +419,7 @@ def run_libsweep_workload(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    X = inputs.config5()
+    X = inputs.logistic_long()
     N, L = X.shape
     Xg = torch.from_numpy(X).to(dev)
     log("generated %d x %d" % (N, L))
@@ -462,7 +462,7 @@ def run_paper_micro_workload(args):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     L = 10000
-    X = inputs.config5(N=16, L=L)
+    X = inputs.logistic_long(N=16, L=L)
     Xg = torch.from_numpy(X).to(dev)
     knn = {}
     for E in range(1, E_MAX + 1):

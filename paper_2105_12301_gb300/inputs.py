@@ -125,22 +125,22 @@ def calcium_lorenz(N, L, seed, tau_decay=5.0, phi=0.9, ar_sigma=0.5,
 
 # --- the five workload recipes ------------------------------------------------
 
-def config1():
+def logistic_16x200():
     """16 coupled-logistic series, L=200 (r~U[3.7,3.9], 20% b~U[0,0.05])."""
     return coupled_logistic(16, 200, 1001, 3.7, 3.9, 0.2, 0.05)
 
 
-def config2(N=1000, L=1000):
+def logistic_noisy(N=1000, L=1000):
     """1,000 x 1,000 coupled logistic, r~U[3.6,3.9], 5% b~U[0,0.1], noise 0.01."""
     return coupled_logistic(N, L, 1002, 3.6, 3.9, 0.05, 0.1, noise=0.01)
 
 
-def config3(N=50000, L=1500, seed=1003):
+def calcium(N=50000, L=1500, seed=1003):
     """Calcium-imaging-shaped all-to-all workload, 50,000 x 1,500."""
     return calcium_lorenz(N, L, seed)
 
 
-def config4_shapes(n_inst=256, seed=1004):
+def uneven_batch_shapes(n_inst=256, seed=1004):
     """(N, L) of the uneven batch: log-uniform ints N in [32, 2048],
     L in [200, 5000]."""
     rng = np.random.default_rng(seed)
@@ -149,12 +149,12 @@ def config4_shapes(n_inst=256, seed=1004):
     return np.minimum(N, 2048), np.minimum(L, 5000)
 
 
-def config4_instance(i, N, L, seed=1004):
+def uneven_batch_instance(i, N, L, seed=1004):
     return coupled_logistic(int(N), int(L), seed * 1000 + i, 3.6, 3.9, 0.05, 0.1,
                             noise=0.02)
 
 
-def config5(N=2000, L=10000):
+def logistic_long(N=2000, L=10000):
     """2,000 x 10,000 coupled logistic for the library-length sweep."""
     return coupled_logistic(N, L, 1005, 3.6, 3.9, 0.05, 0.1, noise=0.01)
 

@@ -1,4 +1,4 @@
-"""Write tests/golden/config1_oracle.json from the FP64 oracle only.
+"""Write tests/golden/logistic_16x200_oracle.json from the FP64 oracle only.
 
 The stored values are the oracle's outputs for the 16 x 200 coupled-logistic
 workload (seed 1001): per-library optimal E over 1..10 by leave-one-out
@@ -20,18 +20,18 @@ from paper_2105_12301_gb300 import inputs  # noqa: E402
 
 
 def main():
-    X = inputs.config1()
+    X = inputs.logistic_16x200()
     E_opt, rho_E = oracle.optimal_E_many(X, 10, 1, 1)
     rho = oracle.ccm_matrix(X, X, E_opt, 1, 0)
     out = {
-        "workload": "config1: 16 coupled logistic maps, L=200, seed 1001",
+        "workload": "logistic_16x200: 16 coupled logistic maps, L=200, seed 1001",
         "E_max": 10, "tau": 1, "Tp_sel": 1, "Tp": 0,
         "E_opt": [int(e) for e in E_opt],
         "rho_E": [[float(v) for v in r] for r in rho_E],
         "rho": [[float(v) for v in r] for r in rho],
     }
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)),
-                        "config1_oracle.json")
+                        "logistic_16x200_oracle.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print(path)

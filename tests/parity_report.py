@@ -102,7 +102,7 @@ def main():
 
     # 16 x 200 coupled logistic, E in 1..10, the full matrix
     t0 = time.time()
-    X = inputs.config1()
+    X = inputs.logistic_16x200()
     rows = list(range(16))
     E_gpu, rep = optimal_E_report(X, rows, 10, 1, 1)
     rep["knn_mismatch"], rep["knn_checked"] = knn_mismatch(X, rows, E_gpu, 1, 0)
@@ -111,7 +111,7 @@ def main():
 
     # 1,000 x 1,000 coupled logistic + noise, E in 1..20
     t0 = time.time()
-    X = inputs.config2()
+    X = inputs.logistic_noisy()
     rows = sorted(rng.choice(1000, 32 if q else 128, replace=False).tolist())
     E_gpu, rep = optimal_E_report(X, rows, 20, 1, 1)
     rep["knn_mismatch"], rep["knn_checked"] = knn_mismatch(X, rows[:16], E_gpu, 1, 0)
@@ -120,7 +120,7 @@ def main():
 
     # 50,000 x 1,500 calcium-shaped, sampled libraries against all targets
     t0 = time.time()
-    X = inputs.config3()
+    X = inputs.calcium()
     rows = sorted(rng.choice(50000, 8 if q else 32, replace=False).tolist())
     E_gpu, rep = optimal_E_report(X, rows, 20, 1, 1)
     rep["knn_mismatch"], rep["knn_checked"] = knn_mismatch(X, rows[:8], E_gpu, 1, 0)
@@ -133,7 +133,7 @@ def main():
     # 2,000 x 10,000 coupled logistic: library-length windows, 1,000 sampled
     # (library, target) pairs per window, E from the full-length simplex
     t0 = time.time()
-    X = inputs.config5()
+    X = inputs.logistic_long()
     Xg = gpu(X)
     E_full, _ = edm.edm_simplex_optimal_E(Xg, 20, 1, 1, with_rho=False)
     E_np = E_full.cpu().numpy()

@@ -51,15 +51,15 @@ def check_ccm(X_lib, Y, E_lib, tau, Tp, precision, tol, lib_rows=None):
     return rho, err
 
 
-def test_config1_optimal_E_and_full_rho_matrix():
-    X = inputs.config1()
+def test_logistic_16x200_optimal_E_and_full_rho_matrix():
+    X = inputs.logistic_16x200()
     E = check_optimal_E(X, 10)
     check_ccm(X, X, E, 1, 0, "fp32", TOL_FP32)
     check_ccm(X, X, E, 1, 0, "bf16", TOL_BF16)
 
 
-def test_config2_sampled_libraries():
-    X = inputs.config2()
+def test_logistic_1000_sampled_libraries():
+    X = inputs.logistic_noisy()
     rows = np.arange(0, 1000, 71)
     E = check_optimal_E(X[rows], 20)
     E_all = np.full(1000, 3, np.int32)
@@ -84,7 +84,7 @@ def test_ragged_counts_tau_and_horizon():
 
 
 def test_mixed_E_in_one_launch():
-    X = inputs.config2(N=40, L=400)
+    X = inputs.logistic_noisy(N=40, L=400)
     E_lib = np.arange(40, dtype=np.int32) % 20 + 1
     check_ccm(X, X, E_lib, 1, 0, "fp32", TOL_FP32)
 
@@ -108,7 +108,7 @@ def test_long_series_gathers_from_global_memory():
 
 
 def test_self_map_equals_simplex():
-    X = inputs.config1()
+    X = inputs.logistic_16x200()
     E_gpu, rho_E = edm.edm_simplex_optimal_E(gpu(X), 6, 1, 0)
     rho = edm.edm_ccm_all(gpu(X), gpu(X), E_gpu, 1, 0).cpu().numpy()
     rho_E = rho_E.cpu().numpy()
@@ -146,7 +146,7 @@ def test_batched_instances_match_single_calls():
 def test_full_size_calcium_workload_sampled():
     # 50,000 x 1,500 as timed by the bench: GPU runs everything, the oracle
     # checks sampled libraries against all 50,000 targets
-    X = inputs.config3()
+    X = inputs.calcium()
     Xg = gpu(X)
     E_gpu, rho_E = edm.edm_simplex_optimal_E(Xg, 20, 1, 1)
     rows = [0, 17, 31337, 49999]
@@ -248,7 +248,7 @@ def test_set_option_rejects_unknown():
 
 def test_per_target_E_rule_matches_oracle():
     # section 3.3: each library is embedded at each target's E
-    X = inputs.config2(N=14, L=350)
+    X = inputs.logistic_noisy(N=14, L=350)
     Y = inputs.coupled_logistic(11, 350, 5150)
     E_tgt = np.array([2, 1, 3, 2, 5, 20, 2, 1, 3, 7, 2], np.int32)
     for prec, tol in (("fp32", TOL_FP32), ("bf16", TOL_BF16)):
@@ -268,7 +268,7 @@ def test_per_target_E_rule_matches_oracle():
 
 
 def test_ccm_all_host_streams_rows_to_pinned_memory():
-    X = inputs.config2(N=300, L=400)
+    X = inputs.logistic_noisy(N=300, L=400)
     E = check_optimal_E(X[:20], 8)
     E_lib = np.resize(E, 300).astype(np.int32)
     Xg = gpu(X)

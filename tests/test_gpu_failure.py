@@ -18,7 +18,7 @@ def test_bounded_wait_gives_up_and_context_stays_usable():
         edm.edm_ctx_sync()
     assert err.value.status == 4            # EDM_ERR_TIMEOUT
     edm.edm_ctx_sync()                      # the flag was cleared by the read
-    X = inputs.config1()[:6]
+    X = inputs.logistic_16x200()[:6]
     Xg = torch.from_numpy(X).cuda()
     E = np.array([2, 3, 1, 2, 4, 2], np.int32)
     rho = edm.edm_ccm_all(Xg, Xg, torch.from_numpy(E).cuda(), 1, 0, "fp32")

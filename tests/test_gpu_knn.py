@@ -30,7 +30,7 @@ def check_knn(X, E, tau, Tp, k=None):
 
 
 def test_embed_matches_oracle():
-    x = inputs.config1()[3]
+    x = inputs.logistic_16x200()[3]
     for E, tau in [(1, 1), (3, 1), (5, 7), (20, 2)]:
         out = edm.edm_embed(gpu(x), E, tau).cpu().numpy()
         np.testing.assert_array_equal(out, oracle.embed(x, E, tau).astype(np.float32))
@@ -38,7 +38,7 @@ def test_embed_matches_oracle():
 
 @pytest.mark.parametrize("E", [1, 2, 3, 5, 8, 13, 20])
 def test_knn_matches_oracle_across_E(E):
-    X = inputs.config1()[:3]
+    X = inputs.logistic_16x200()[:3]
     check_knn(X, E, 1, 0)
     check_knn(X, E, 2, 1)
 
@@ -78,7 +78,7 @@ def test_knn_repeated_pattern_near_ties():
 
 
 def test_knn_many_series_full_table():
-    X = inputs.config2(N=24, L=300)
+    X = inputs.logistic_noisy(N=24, L=300)
     check_knn(X, 4, 1, 0)
 
 
@@ -95,7 +95,7 @@ def test_knn_long_series_sampled_rows():
 
 
 def test_knn_rejects_bad_arguments():
-    X = gpu(inputs.config1()[:1])
+    X = gpu(inputs.logistic_16x200()[:1])
     with pytest.raises(edm.EdmError):
         edm.edm_knn(X, 21, 1, 0)          # E above EDM_E_MAX
     with pytest.raises(edm.EdmError):

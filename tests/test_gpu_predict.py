@@ -33,7 +33,7 @@ def check_predictions(X_lib, Y, E, tgt, tau, Tp):
 
 
 def test_self_forecast_matches_oracle():
-    X = inputs.config2(N=12, L=400)
+    X = inputs.logistic_noisy(N=12, L=400)
     E = np.array([1, 2, 3, 4, 5, 6, 2, 3, 1, 8, 20, 2], np.int32)
     check_predictions(X, X, E, None, 1, 1)
 
@@ -48,7 +48,7 @@ def test_cross_forecast_with_target_map_tau_and_ragged_groups():
 
 
 def test_bad_target_index_gives_nan_row_and_error():
-    X = inputs.config1()[:3]
+    X = inputs.logistic_16x200()[:3]
     E = gpu(np.array([2, 2, 2], np.int32))
     tgt = gpu(np.array([0, 7, 1], np.int32))   # 7 is out of range for 3 targets
     pred = edm.edm_predict(gpu(X), gpu(X), E, tgt, 1, 0)

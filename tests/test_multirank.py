@@ -22,7 +22,7 @@ def _worker(rank, size, port, q):
     import torch.distributed as dist
     r, n = ranks.init("gloo")
     seed = ranks.problem_seed(1003, r)
-    X = inputs.config3(N=8, L=64, seed=seed)
+    X = inputs.calcium(N=8, L=64, seed=seed)
     m = ranks.max_over_ranks(10.0 + r)
     ranks.barrier()
     q.put((r, n, seed, float(X[0, 0]), m))

@@ -211,7 +211,7 @@ def test_simplex_logistic_map_high_skill():
 
 
 def test_ccm_self_map_equals_simplex():
-    X = inputs.config1()
+    X = inputs.logistic_16x200()
     for i in (0, 5):
         for E in (1, 3, 6):
             row = oracle.ccm_row(X[i], X[i], E, 1, 0)

@@ -50,8 +50,8 @@ def compare(got, ref):
 
 
 def test_noalloc_matches_context_path_on_two_calls_in_a_row():
-    A = torch.from_numpy(inputs.config1()).cuda()                    # 16 x 200
-    B = torch.from_numpy(inputs.config2(N=300, L=700)).cuda()        # 300 x 700
+    A = torch.from_numpy(inputs.logistic_16x200()).cuda()                    # 16 x 200
+    B = torch.from_numpy(inputs.logistic_noisy(N=300, L=700)).cuda()        # 300 x 700
     ref_a = reference(A, 10, 1, 1)
     ref_b = reference(B, 20, 1, 1)
     compare(call_noalloc_abi(A, 10, 1, 1), ref_a)
