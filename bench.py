@@ -274,6 +274,22 @@ def run_gb300(args):
         "avg_launch_ms": lk_avg_ms,
         "nominal_peak_at_sampled_clock_gbs": (152 * 128 * clk["sm_mhz"] * 1e6 / 1e9) if clk else None,
     }
+    # the optimal-E sweep against FP32 issue: 3 lane-ops (sub, fma, compare)
+    # per candidate, query row and E; peak = SMs x 128 lanes x sampled clock
+    sw_ms = prof["sweep_kernel"][0] / args.steps
+    sweep_ops = 3.0 * N * sum(max(0, L - (e - 1) * TAU - TP_SEL) * max(0, L - (e - 1) * TAU - TP_SEL - 1)
+                              for e in range(1, E_MAX + 1)
+                              if L - (e - 1) * TAU - TP_SEL >= e + 2)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = n_sm * 128 * (clk["sm_mhz"] if clk else 2070.0) * 1e6
+    roofline_sweep = {
+        "bound": "alu", "kernel": "sweep_kernel",
+        "achieved": sweep_ops / (sw_ms / 1e3) / 1e12 if sw_ms > 0 else None,
+        "peak": alu_peak / 1e12, "unit": "Tops/s (FP32 lane-ops)",
+        "frac": (sweep_ops / (sw_ms / 1e3)) / alu_peak if sw_ms > 0 else None,
+        "peak_source": "derived: SMs x 128 FP32 lanes x sampled SM clock",
+        "algorithmic_ops_per_step": sweep_ops,
+    }
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": size,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
@@ -286,6 +302,7 @@ def run_gb300(args):
         "knn_rows_per_s": knn_rows_per_s,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
         "roofline": roofline,
+        "roofline_sweep": roofline_sweep,
         "E_opt_hist": np.bincount(E_np, minlength=E_MAX + 1)[1:].tolist(),
     }
 
