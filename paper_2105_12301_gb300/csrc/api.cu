@@ -104,7 +104,7 @@ static bool series_len_ok(int L) { return L >= 2 && L <= EDM_L_MAX; }
 // whose neighbour tables fit the table budget; each chunk is grouped by E
 // (launch_group_libs), its tables are built in the grouped layout, then the
 // lookup runs over every (group, target tile).
-static int ccm_chunk(edm_ctx *ctx, int N_lib, size_t slot, int G) {
+static int ccm_chunk(edm_ctx *ctx, int N_lib, size_t slot) {
     const size_t per = std::max<size_t>(1, ctx->table_budget / slot);
     return static_cast<int>(std::max<size_t>(1, std::min<size_t>(N_lib, per)));
 }
@@ -117,7 +117,7 @@ static size_t ccm_workspace_bytes(edm_ctx *ctx, int N_lib, int N_tgt, int L, int
     const size_t slot = ccm_slot_bytes(L, tau, Tp);
     if (slot == 0) return yt_bytes + mean_bytes + 2 * sums_bytes;
     const int G = lookup_group(prec);
-    const int chunk = ccm_chunk(ctx, N_lib, slot, G);
+    const int chunk = ccm_chunk(ctx, N_lib, slot);
     return yt_bytes + mean_bytes + 2 * sums_bytes + groups_bytes(chunk, G) +
            static_cast<size_t>(groups_max(chunk, G)) * G * slot;
 }
@@ -142,7 +142,7 @@ static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, in
     const size_t slot = ccm_slot_bytes(L, tau, Tp);
     if (slot == 0) return set_error(ctx, EDM_ERR_INVALID_ARG, "series too short");
     const int G = lookup_group(prec);
-    const int chunk = ccm_chunk(ctx, N_lib, slot, G);
+    const int chunk = ccm_chunk(ctx, N_lib, slot);
     edm_status st = ws_reserve(ctx, ccm_workspace_bytes(ctx, N_lib, N_tgt, L, tau, Tp, prec));
     if (st != EDM_OK) return st;
     uint8_t *base = static_cast<uint8_t *>(ctx->ws);
@@ -686,7 +686,7 @@ edm_status edm_predict(edm_ctx *ctx, const float *X_lib, int N_lib, const float 
     const size_t slot = ccm_slot_bytes(L, tau, Tp);
     if (slot == 0) return set_error(ctx, EDM_ERR_INVALID_ARG, "series too short");
     const int G = LK_GROUP_FP32;
-    const int chunk = ccm_chunk(ctx, N_lib, slot, G);
+    const int chunk = ccm_chunk(ctx, N_lib, slot);
     edm_status st = ws_reserve(ctx, groups_bytes(chunk, G) +
                                         static_cast<size_t>(groups_max(chunk, G)) * G * slot);
     if (st != EDM_OK) return st;
