@@ -339,6 +339,20 @@ __device__ __forceinline__ void lookup_pair_half(const uint8_t *blk, const uint3
     }
 }
 
+// Position in the ring of table stages: the stage and the parity of the
+// ring's current pass (kept incrementally; the stage count is a run-time
+// value, so no division per stage).
+struct RingPos {
+    int s = 0;
+    uint32_t ph = 0;
+    __device__ __forceinline__ void next(int stages) {
+        if (++s == stages) {
+            s = 0;
+            ph ^= 1u;
+        }
+    }
+};
+
 // Gather + accumulate one group whose k = K is a compile-time value: warps
 // take pairs warp, warp + NC, ... of each stage; a pair's observations are
 // read once and serve every member of the group.  All G slots are processed
@@ -346,7 +360,7 @@ __device__ __forceinline__ void lookup_pair_half(const uint8_t *blk, const uint3
 template <int K, bool BF16, bool SMEM_TILE, bool HALF>
 __device__ __forceinline__ void consume_group(const LookupArgs &a, const uint8_t *tile,
                                               const uint8_t *stages, uint64_t *full,
-                                              uint64_t *empty, int &seq, int n, int t0,
+                                              uint64_t *empty, RingPos &rp, int n, int t0,
                                               PairMoments<BF16> (&pm)[LkCfg<BF16>::G]) {
     using C = LkCfg<BF16>;
     constexpr int PB = table_pair_bytes(K);
@@ -358,9 +372,8 @@ __device__ __forceinline__ void consume_group(const LookupArgs &a, const uint8_t
     const int npairs = (n + 1) >> 1;
     if (HALF) {
         for (int p0 = 0; p0 < npairs; p0 += CP) {
-            const int s = seq % a.stages;
-            const uint32_t par = (seq / a.stages) & 1;
-            mbar_wait_bounded(&full[s], par, a.flags);
+            const int s = rp.s;
+            mbar_wait_bounded(&full[s], rp.ph, a.flags);
             const uint8_t *st = stages + static_cast<size_t>(s) * a.stage_bytes;
             const int pairs = min(CP, npairs - p0);
             const int ybase = t0 + a.Tp + 2 * p0 + h;
@@ -373,14 +386,13 @@ __device__ __forceinline__ void consume_group(const LookupArgs &a, const uint8_t
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
-            ++seq;
+            rp.next(a.stages);
         }
         return;
     }
     for (int p0 = 0; p0 < npairs; p0 += CP) {
-        const int s = seq % a.stages;
-        const uint32_t par = (seq / a.stages) & 1;
-        mbar_wait_bounded(&full[s], par, a.flags);
+        const int s = rp.s;
+        mbar_wait_bounded(&full[s], rp.ph, a.flags);
         const uint8_t *st = stages + static_cast<size_t>(s) * a.stage_bytes;
         const int pairs = min(CP, npairs - p0);
         const int ybase = t0 + a.Tp + 2 * p0;
@@ -395,7 +407,7 @@ __device__ __forceinline__ void consume_group(const LookupArgs &a, const uint8_t
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
-        ++seq;
+        rp.next(a.stages);
     }
 }
 
@@ -452,7 +464,8 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
                                   static_cast<uint32_t>(tile_bytes - off < 32768 ? tile_bytes - off : 32768),
                                   tbar);
             }
-            int seq = 0;
+            RingPos rp;
+            bool first_pass = true;  // the stages are empty until the ring wraps
             for (int gi = g0; gi < g1; ++gi) {
                 const int E = a.grp.E[gi];
                 if (E == 0) continue;
@@ -462,13 +475,14 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
                 const int CP = a.stage_bytes / GPB;
                 const uint8_t *src = a.tables + a.grp.off[gi];
                 for (int p0 = 0; p0 < npairs; p0 += CP) {
-                    const int s = seq % a.stages, j = seq / a.stages;
-                    if (j > 0) mbar_wait_bounded(&empty[s], (j - 1) & 1, a.flags);
+                    const int s = rp.s;
+                    if (!first_pass) mbar_wait_bounded(&empty[s], rp.ph ^ 1u, a.flags);
                     const uint32_t bytes = static_cast<uint32_t>(min(CP, npairs - p0) * GPB);
                     mbar_arrive_expect_tx(&full[s], bytes);
                     bulk_copy_g2s(stages + static_cast<size_t>(s) * a.stage_bytes,
                                   src + static_cast<size_t>(p0) * GPB, bytes, &full[s]);
-                    ++seq;
+                    rp.next(a.stages);
+                    if (rp.s == 0) first_pass = false;
                 }
             }
         }
@@ -537,7 +551,8 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
     // -------------------- consumers
     const uint8_t *tile = SMEM_TILE ? tile_s : tile_g;
     if (SMEM_TILE) mbar_wait_bounded(tbar, 0, a.flags);
-    int seq = 0, done = 0;
+    RingPos rp;
+    int done = 0;
     PairMoments<BF16> pm[G];
     for (int gi = g0; gi < g1; ++gi) {
         const int E = a.grp.E[gi];
@@ -551,7 +566,7 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
                 pm[m].s[c] = pm[m].ss[c] = pm[m].sy[c] = f2(0.f, 0.f);
         switch (E + 1) {
 #define EDM_CASE(k) \
-    case k: consume_group<k, BF16, SMEM_TILE, HALF>(a, tile, stages, full, empty, seq, n, t0, pm); break;
+    case k: consume_group<k, BF16, SMEM_TILE, HALF>(a, tile, stages, full, empty, rp, n, t0, pm); break;
             EDM_CASE(2) EDM_CASE(3) EDM_CASE(4) EDM_CASE(5) EDM_CASE(6) EDM_CASE(7) EDM_CASE(8)
             EDM_CASE(9) EDM_CASE(10) EDM_CASE(11) EDM_CASE(12) EDM_CASE(13) EDM_CASE(14)
             EDM_CASE(15) EDM_CASE(16) EDM_CASE(17) EDM_CASE(18) EDM_CASE(19) EDM_CASE(20)
