@@ -44,6 +44,8 @@ def _load():
         lib.oracle_simplex_rho.argtypes = [f32p] + [c_int] * 4
         lib.oracle_simplex_rho.restype = ctypes.c_double
         lib.oracle_optimal_E.argtypes = [f32p] + [c_int] * 4 + [i32p, f64p]
+        lib.oracle_argmax_E.argtypes = [f64p, c_int]
+        lib.oracle_argmax_E.restype = c_int
         for name in ("oracle_embed", "oracle_knn", "oracle_knn_row",
                      "oracle_predict", "oracle_ccm_row", "oracle_optimal_E"):
             getattr(lib, name).restype = c_int
@@ -134,6 +136,13 @@ def optimal_E(x, E_max, tau, Tp_sel):
     _check(_load().oracle_optimal_E(x, x.shape[0], E_max, tau, Tp_sel, e, rho),
            "optimal_E")
     return int(e[0]), rho
+
+
+def argmax_E(rho_E):
+    """E* (1-based) of the skills rho_E[E-1]: NaN below every number, ties to
+    the smaller E, 1 when all are NaN."""
+    r = np.ascontiguousarray(rho_E, np.float64)
+    return int(_load().oracle_argmax_E(r, r.shape[0]))
 
 
 def ccm_row(x_lib, Y, E, tau, Tp):

@@ -253,29 +253,47 @@ double oracle_simplex_rho(const float *X, int L, int E, int tau, int Tp)
     return rho;
 }
 
+/* Argmax of the skills rho_E[0..E_max-1] of E = 1..E_max (section 3.3 names
+ * the optimal E without defining it; the reading is argmax rho_E).  A NaN skill
+ * ranks below every number; among equal skills the smallest E wins; when every
+ * skill is NaN the result is 1. */
+int oracle_argmax_E(const double *rho_E, int E_max)
+{
+    int best_E = 1;
+    double best = NAN;
+    for (int E = 1; E <= E_max; ++E) {
+        double r = rho_E[E - 1];
+        if (isnan(r))
+            continue;
+        if (isnan(best) || r > best) { /* strictly greater: ties keep the smaller E */
+            best = r;
+            best_E = E;
+        }
+    }
+    return best_E;
+}
+
 /* Optimal embedding dimension by simplex projection over E = 1..E_max
  * (named but not specified in section 3.3; the reading is leave-one-out
  * simplex at horizon Tp_sel).  rho_E[E-1] receives each skill (NaN when E
- * leaves fewer than E+2 points); E_opt = argmax with NaN below every
- * number and ties to the smallest E. */
+ * leaves fewer than E+2 points); E_opt is oracle_argmax_E of them.  rho_E may
+ * be NULL. */
 int oracle_optimal_E(const float *X, int L, int E_max, int tau, int Tp_sel,
                      int32_t *E_opt, double *rho_E)
 {
     if (!X || !E_opt || L < 2 || E_max < 1 || tau < 1 || Tp_sel < 0)
         return ORACLE_EINVAL;
-    int best_E = 1;
-    double best = NAN;
+    double *r = (double *)malloc(sizeof(double) * (size_t)E_max);
+    if (!r)
+        return ORACLE_ENOMEM;
     for (int E = 1; E <= E_max; ++E) {
-        double r = NAN;
+        r[E - 1] = NAN;
         if (knn_args_ok(X, L, E, tau, Tp_sel, E + 1))
-            r = oracle_simplex_rho(X, L, E, tau, Tp_sel);
+            r[E - 1] = oracle_simplex_rho(X, L, E, tau, Tp_sel);
         if (rho_E)
-            rho_E[E - 1] = r;
-        if (!isnan(r) && (isnan(best) || r > best)) {
-            best = r;
-            best_E = E;
-        }
+            rho_E[E - 1] = r[E - 1];
     }
-    *E_opt = best_E;
+    *E_opt = oracle_argmax_E(r, E_max);
+    free(r);
     return ORACLE_OK;
 }

@@ -294,6 +294,40 @@ def test_optimal_E_nan_and_ties():
     assert np.all(np.isfinite(rho[n >= np.arange(1, 11) + 2]))
 
 
+def test_argmax_E_tie_and_nan_rule():
+    # Hand-written skills with the expected E* from the stated rule: the
+    # largest skill wins, a NaN ranks below every number, equal skills go to
+    # the smaller E, and all-NaN gives 1.  Ties to the larger E (>=), a NaN
+    # that wins, or a 0-based result each fail one of these.
+    nan = float("nan")
+    cases = [
+        ([0.5, 0.5, 0.3], 1),
+        ([0.1, 0.7, 0.7, 0.2], 2),
+        ([0.2, 0.9, 0.4, 0.9, 0.9], 2),
+        ([nan, 0.2, 0.2], 2),
+        ([nan, nan, -0.3, -0.3], 3),
+        ([-0.5, nan, -0.5], 1),
+        ([0.3, nan, 0.8], 3),
+        ([nan, nan, nan], 1),
+        ([-1.0], 1),
+        ([0.0, -0.0], 1),                   # -0.0 == 0.0 is a tie
+        ([0.25, 0.25 + 2.0 ** -52, 0.25], 2),   # one ulp above is not a tie
+    ]
+    for rho, want in cases:
+        assert oracle.argmax_E(np.array(rho)) == want, (rho, want)
+
+
+def test_optimal_E_uses_the_argmax_rule():
+    # the E* that oracle_optimal_E reports is the rule applied to the skills
+    # it reports, on data with NaN skills at large E (short series)
+    for seed, L in ((5, 14), (6, 40), (7, 200)):
+        x = inputs.coupled_logistic(1, L, seed)[0]
+        E, rho = oracle.optimal_E(x, 12, 1, 1)
+        finite = np.where(np.isnan(rho), -np.inf, rho)
+        want = int(np.flatnonzero(finite == finite.max())[0]) + 1 if np.isfinite(finite.max()) else 1
+        assert E == want
+
+
 def test_constant_target_gives_nan():
     X = inputs.coupled_logistic(1, 80, 2)
     assert math.isnan(oracle.ccm_row(X[0], np.full(80, 2.0, np.float32), 2, 1, 0)[0])
