@@ -11,9 +11,12 @@ workload (50,000 series x 1,500 steps, inputs resident in HBM):
 
 Prints one JSON line.  `value` is CCM pairs/s of the plain FP32 path, timed
 with CUDA events on the launching stream over K steps; the mixed-precision
-form (BF16 target storage) is reported beside it under "mixed".  With N > 1
-(torchrun) every rank runs its own problem of the same shape (weak scaling,
-no data exchange); the step time is the maximum over ranks.
+forms are reported beside it: "mixed" (FP32 distances and moments, targets
+stored as scaled FP16) and "mixed_bf16" (targets stored as BF16), each with
+its measured |drho| against the plain run and the FP64 oracle.  With N > 1
+(torchrun) the one problem is split by library rows, one contiguous block per
+rank with every series replicated (strong scaling, no data exchange); the
+step time is the maximum over ranks.
 """
 import argparse
 import json
@@ -59,7 +62,8 @@ def workload_config(name, N, L, world_size):
         "n_series": N, "series_len": L, "pairs_per_step": N * N,
         "E_range": [1, E_MAX], "tau": TAU, "Tp": TP, "Tp_sel": TP_SEL,
         "libraries": "all series", "targets": "all series",
-        "parallelism": "independent problem per GPU" if world_size > 1 else "single GPU",
+        "parallelism": ("library rows split in contiguous blocks, one per GPU, all series "
+                        "replicated (no exchange)") if world_size > 1 else "single GPU",
         "l2": "inputs larger than L2 (300 MB series, 10 GB rho, GB-scale tables); no flush",
     }
 
@@ -127,23 +131,37 @@ class ClockSampler:
 
 # --------------------------------------------------------- CPU baseline
 
+def sample_rows(N, n_libs):
+    return np.linspace(0, N - 1, n_libs).astype(int)
+
+
 def cpu_sample(X, n_libs, threads):
-    """The FP64 oracle on n_libs libraries x all targets (optimal E included);
-    returns (pairs/s, seconds)."""
+    """The FP64 oracle on n_libs libraries (sample_rows) x all targets,
+    optimal E included; returns (pairs/s, seconds, [(E*, rho row)])."""
     import oracle
     from concurrent.futures import ThreadPoolExecutor
 
-    rows = np.linspace(0, X.shape[0] - 1, n_libs).astype(int)
+    rows = sample_rows(X.shape[0], n_libs)
 
     def one(i):
         e, _ = oracle.optimal_E(X[i], E_MAX, TAU, TP_SEL)
-        return oracle.ccm_row(X[i], X, e, TAU, TP)
+        return e, oracle.ccm_row(X[i], X, e, TAU, TP)
 
     t0 = time.perf_counter()
     with ThreadPoolExecutor(threads) as ex:
-        list(ex.map(one, rows))
+        res = list(ex.map(one, rows))
     dt = time.perf_counter() - t0
-    return n_libs * X.shape[0] / dt, dt
+    return n_libs * X.shape[0] / dt, dt, res
+
+
+def drho_stats(a, b):
+    """max and 99th percentile of |a - b| over the pairs where both are
+    numbers, and how many pairs that is."""
+    ok = np.isfinite(a) & np.isfinite(b)
+    d = np.abs(a[ok].astype(np.float64) - b[ok].astype(np.float64))
+    return {"max": float(d.max(initial=0.0)),
+            "p99": float(np.percentile(d, 99)) if d.size else 0.0,
+            "pairs": int(d.size)}
 
 
 def run_reference(args):
@@ -159,7 +177,7 @@ def run_reference(args):
         cpu_sample(X, max(1, threads // 4), threads)
     vals, secs = [], []
     for _ in range(args.steps):
-        v, dt = cpu_sample(X, n_libs, threads)
+        v, dt, _ = cpu_sample(X, n_libs, threads)
         vals.append(v)
         secs.append(dt)
     value = float(np.mean(vals))
@@ -169,7 +187,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * float(np.mean(secs)), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args.workload, N, L, 1),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample},
@@ -195,14 +213,17 @@ def run_gb300(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     N, L = workload(args.workload)
-    X = inputs.calcium(N, L, seed=ranks.problem_seed(1003, rank))
+    X = inputs.calcium(N, L)
     Xg = torch.from_numpy(X).to(dev)
-    rho = torch.empty((N, N), dtype=torch.float32, device=dev)
+    # one problem split by library rows (every rank holds all series)
+    b, e = ranks.row_block(N, rank, size)
+    Xlib = Xg[b:e]
+    rho = torch.empty((e - b, N), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step(prec):
-        E_opt, _ = edm.edm_simplex_optimal_E(Xg, E_MAX, TAU, TP_SEL, with_rho=False)
-        edm.edm_ccm_all(Xg, Xg, E_opt, TAU, TP, prec, out=rho)
+        E_opt, _ = edm.edm_simplex_optimal_E(Xlib, E_MAX, TAU, TP_SEL, with_rho=False)
+        edm.edm_ccm_all(Xlib, Xg, E_opt, TAU, TP, prec, out=rho)
         return E_opt
 
     def timed(prec, warmup, steps, profile=False):
@@ -235,14 +256,22 @@ def run_gb300(args):
     ms, launches, E_opt = timed(args.precision, args.warmup, args.steps, profile=True)
     clk = clocks.stop()
     ms_max = ranks.max_over_ranks(ms, dev)
-    pairs = float(N) * N
-    value = size * pairs / (ms_max / 1e3)
+    pairs = float(N) * N                  # the whole job: every rank's row block
+    value = pairs / (ms_max / 1e3)
 
     # per-kernel device times of the timed steps
-    prof = {k: edm.edm_profile_read(k, dev) for k in ("sweep_kernel", "simplex_kernel", "simplex_finish_kernel",
+    prof = {k: edm.edm_profile_read(k, dev) for k in ("sweep_kernel", "sweep_long_kernel", "simplex_finish_kernel",
                                       "ccm_table_kernel", "lookup_kernel", "target_store_kernel",
-                                      "target_mean_kernel")}
+                                      "target_mean_kernel", "target_sums_kernel",
+                                      "group_libs_kernel")}
     edm.edm_profile_enable(False, dev)
+    # the rows of the FP64 band and brute-force fallbacks, counted on one
+    # extra untimed step
+    edm.edm_set_option("diagnostics", 1, dev)
+    edm.edm_fallback_counts(dev)
+    step(args.precision)
+    fb_band, fb_brute = edm.edm_fallback_counts(dev)
+    edm.edm_set_option("diagnostics", 0, dev)
     E_np = E_opt.cpu().numpy().astype(np.int64)
     n_lib = L - (E_np - 1) * TAU - TP                       # rows per library table
     k_lib = E_np + 1
@@ -250,14 +279,14 @@ def run_gb300(args):
     # algorithmic shared-memory gather bytes of one step: one stored target
     # value per (query row, neighbour) of every (library, target) pair; the
     # table broadcast and the observation reads are overhead, not counted
-    lookup_bytes = float(np.sum(n_lib * k_lib)) * N * bpv
+    lookup_bytes = float(np.sum(n_lib * k_lib)) * N * bpv     # this rank's libraries
     lk_ms, lk_n = prof["lookup_kernel"]
     lk_avg_ms = lk_ms / max(lk_n, 1)
     achieved_gbs = lookup_bytes * args.steps / (lk_ms / 1e3) / 1e9 if lk_ms > 0 else None
-    sweep_rows = sum(max(0, L - (e - 1) * TAU - TP_SEL) for e in range(1, E_MAX + 1)
-                     if L - (e - 1) * TAU - TP_SEL >= e + 2) * N
+    sweep_rows = sum(max(0, L - (E - 1) * TAU - TP_SEL) for E in range(1, E_MAX + 1)
+                     if L - (E - 1) * TAU - TP_SEL >= E + 2) * (e - b)
     table_rows = float(np.sum(n_lib))
-    knn_ms = (prof["sweep_kernel"][0] + prof["simplex_kernel"][0] +
+    knn_ms = (prof["sweep_kernel"][0] + prof["sweep_long_kernel"][0] +
               prof["ccm_table_kernel"][0]) / args.steps
     knn_rows_per_s = (sweep_rows + table_rows) / (knn_ms / 1e3) if knn_ms > 0 else None
     lookup_src = os.path.join(ROOT, "paper_2105_12301_gb300", "csrc", "lookup.cu")
@@ -277,9 +306,9 @@ def run_gb300(args):
     # the optimal-E sweep against FP32 issue: 3 lane-ops (sub, fma, compare)
     # per candidate, query row and E; peak = SMs x 128 lanes x sampled clock
     sw_ms = prof["sweep_kernel"][0] / args.steps
-    sweep_ops = 3.0 * N * sum(max(0, L - (e - 1) * TAU - TP_SEL) * max(0, L - (e - 1) * TAU - TP_SEL - 1)
-                              for e in range(1, E_MAX + 1)
-                              if L - (e - 1) * TAU - TP_SEL >= e + 2)
+    sweep_ops = 3.0 * (e - b) * sum(max(0, L - (E - 1) * TAU - TP_SEL) * max(0, L - (E - 1) * TAU - TP_SEL - 1)
+                                    for E in range(1, E_MAX + 1)
+                                    if L - (E - 1) * TAU - TP_SEL >= E + 2)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak = n_sm * 128 * (clk["sm_mhz"] if clk else 2070.0) * 1e6
     roofline_sweep = {
@@ -293,7 +322,7 @@ def run_gb300(args):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": size,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f32+bf16-targets",
         "data": "synthetic",
         "config": workload_config(args.workload, N, L, size),
@@ -304,29 +333,79 @@ def run_gb300(args):
         "roofline": roofline,
         "roofline_sweep": roofline_sweep,
         "E_opt_hist": np.bincount(E_np, minlength=E_MAX + 1)[1:].tolist(),
+        "fp64_fallbacks": {"band_rows": fb_band, "brute_rows": fb_brute,
+                           "rows_selected": int(sweep_rows + table_rows),
+                           "note": "query rows (per E) whose exact neighbour set needed the FP64 "
+                                   "band, and of those a full FP64 scan; one untimed step, "
+                                   "this rank's libraries"},
     }
 
+    cores = os.cpu_count() or 1
+    rows = sample_rows(e - b, 3 * cores)        # the libraries the oracle samples (this block)
+    plain_rows = rho[torch.from_numpy(rows).to(dev)].cpu().numpy()
+
+    def lookup_roofline(prof_run, bytes_per_value, clk_run):
+        lk_ms_run, lk_n_run = prof_run["lookup_kernel"]
+        lk_bytes = float(np.sum(n_lib * k_lib)) * N * bytes_per_value
+        ach = lk_bytes * steps_run[0] / (lk_ms_run / 1e3) / 1e9 if lk_ms_run > 0 else None
+        return {"bound": "smem", "kernel": "lookup_kernel", "achieved": ach,
+                "peak": smem_peak_gbs, "unit": "GB/s",
+                "frac": ach / smem_peak_gbs if ach and smem_peak_gbs else None,
+                "traffic": None,
+                "peak_source": roofline["peak_source"],
+                "algorithmic_bytes_per_launch": lk_bytes * steps_run[0] / max(lk_n_run, 1),
+                "avg_launch_ms": lk_ms_run / max(lk_n_run, 1),
+                "nominal_peak_at_sampled_clock_gbs":
+                    (152 * 128 * clk_run["sm_mhz"] * 1e6 / 1e9) if clk_run else None}
+
+    steps_run = [0]
+    mixed_rows = {}
     if args.mixed and args.precision == "fp32":
-        ms_m, _, _ = timed("bf16", 1, max(1, args.steps - 1))
-        ms_m = ranks.max_over_ranks(ms_m, dev)
-        out["mixed"] = {"value": size * pairs / (ms_m / 1e3), "unit": UNIT, "ms_per_step": ms_m,
-                        "dtype": "f32+bf16-targets", "tolerance": "|drho| <= 1e-3 (tests)"}
+        # the 16-bit target storages, each on its own timed steps with its own
+        # clock record and per-kernel split
+        for key, prec, dtype in (("mixed", "fp16", "f32+fp16-targets"),
+                                 ("mixed_bf16", "bf16", "f32+bf16-targets")):
+            steps_m = max(3, args.steps // 4)
+            steps_run[0] = steps_m
+            clocks_m = ClockSampler(local)
+            clocks_m.start()
+            ms_m, _, E_m = timed(prec, 1, steps_m, profile=True)
+            clk_m = clocks_m.stop()
+            ms_m = ranks.max_over_ranks(ms_m, dev)
+            prof_m = {k: edm.edm_profile_read(k, dev) for k in prof}
+            edm.edm_profile_enable(False, dev)
+            assert torch.equal(E_m.cpu(), E_opt.cpu())
+            mixed_rows[key] = rho[torch.from_numpy(rows).to(dev)].cpu().numpy()
+            out[key] = {
+                "value": pairs / (ms_m / 1e3), "unit": UNIT, "ms_per_step": ms_m,
+                "steps": steps_m, "dtype": dtype, "clocks": clk_m,
+                "kernel_ms_per_step": {k: v[0] / steps_m for k, v in prof_m.items() if v[1]},
+                "roofline": lookup_roofline(prof_m, 2, clk_m),
+                "drho_vs_plain": drho_stats(mixed_rows[key], plain_rows),
+                "drho_sample": "%d libraries (evenly spaced) x all %d targets" % (len(rows), N),
+            }
+        out["mixed"]["tolerance"] = ("FP16 target storage: |drho| <= 5e-4 against the FP64 oracle "
+                                     "(tests); drho_vs_plain / drho_vs_oracle measured here")
+        out["mixed_bf16"]["tolerance"] = ("BF16 target storage: |drho| <= 1e-3 against the FP64 "
+                                          "oracle for >= 300 library points (tests)")
 
     if args.e2e:
-        # public API end to end: pinned host series in, rho out, every step
+        # public API end to end, every step: pinned host series up
+        # (edm_upload_series), optimal E, tables, lookup, rho streamed down
+        # block by block as it is finished (edm_ccm_all_host)
         X_h = torch.from_numpy(X).pin_memory()
-        rho_h = torch.empty((N, N), dtype=torch.float32, pin_memory=True)
-        steps_e2e = max(1, min(args.steps, 2))
+        rho_h = torch.empty((e - b, N), dtype=torch.float32, pin_memory=True)
+        steps_e2e = max(1, args.steps)
 
         def e2e_step():
-            # series up; rho streamed down block by block as it is finished
-            Xg.copy_(X_h, non_blocking=True)
-            E_opt, _ = edm.edm_simplex_optimal_E(Xg, E_MAX, TAU, TP_SEL, with_rho=False)
-            edm.edm_ccm_all_host(Xg, Xg, E_opt, rho, rho_h, TAU, TP, args.precision)
+            edm.edm_upload_series(X_h, Xg)
+            E_opt, _ = edm.edm_simplex_optimal_E(Xlib, E_MAX, TAU, TP_SEL, with_rho=False)
+            edm.edm_ccm_all_host(Xlib, Xg, E_opt, rho, rho_h, TAU, TP, args.precision)
 
         e2e_step()
         torch.cuda.synchronize(dev)
         ranks.barrier()
+        launches_e0 = edm.edm_kernel_launches(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -335,19 +414,30 @@ def run_gb300(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ms_e = ranks.max_over_ranks(e0.elapsed_time(e1) / steps_e2e, dev)
-        out["e2e"] = {"value": size * pairs / (ms_e / 1e3), "unit": UNIT,
-                      "h2d_bytes_per_step": int(X_h.numel() * 4),
-                      "d2h_bytes_per_step": int(rho_h.numel() * 4), "ms_per_step": ms_e,
-                      "steps": steps_e2e}
+        edm.edm_ctx_sync(dev)
+        out["e2e"] = {"value": pairs / (ms_e / 1e3), "unit": UNIT,
+                      "h2d_bytes_per_step": int(X_h.numel() * 4) * size,    # every rank uploads all series
+                      "d2h_bytes_per_step": int(N) * N * 4,                # all row blocks together
+                      "ms_per_step": ms_e,
+                      "steps": steps_e2e,
+                      "gpu_launches": int(edm.edm_kernel_launches(dev) - launches_e0),
+                      "api": "edm_upload_series -> edm_simplex_optimal_E -> edm_ccm_all_host"}
         del rho_h
 
     if args.cpu_baseline and rank == 0 and size == 1:
-        cores = os.cpu_count() or 1
-        v, dt = cpu_sample(X, cores * 3, cores)
+        v, dt, res = cpu_sample(X, len(rows), cores)
         out["cpu_baseline"] = {
             "value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d libraries x all %d targets (optimal E over 1..%d + CCM row), %.1f s"
-                      % (cores * 3, N, E_MAX, dt)}
+                      % (len(rows), N, E_MAX, dt)}
+        # the same libraries against the GPU rows of the timed runs, where the
+        # oracle's E* equals the GPU's (the oracle used its own E*)
+        same = [r for r, (e, _) in enumerate(res) if e == int(E_np[rows[r]])]
+        ref = np.stack([res[r][1] for r in same]) if same else np.zeros((0, N))
+        out["drho_vs_oracle"] = {"libraries": len(same), "fp32": drho_stats(plain_rows[same], ref)}
+        for key in mixed_rows:
+            out["drho_vs_oracle"][out[key]["dtype"]] = drho_stats(mixed_rows[key][same], ref)
+            out[key]["drho_vs_oracle"] = out["drho_vs_oracle"][out[key]["dtype"]]
     if rank == 0:
         print(json.dumps(out), flush=True)
 

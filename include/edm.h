@@ -54,11 +54,21 @@ typedef enum edm_status {
     EDM_ERR_INTERNAL = 5     /* an internal consistency check failed       */
 } edm_status;
 
-/* Storage of the target series inside edm_ccm_all.  Library distances,
- * weights and the Pearson moments are FP32 in both modes. */
+/* Storage of the target series inside the CCM calls.  Library distances,
+ * weights and the Pearson moments are FP32 in every mode; the 16-bit modes
+ * halve the bytes of every gathered target value.  Each target is centred on
+ * its FP64 mean before it is stored.
+ *   EDM_BF16_TARGETS: 8 significant bits.  Measured |rho - rho_FP64| stays
+ *     below 1e-3 for library lengths of 300 points or more; at 100 points it
+ *     reaches about 1.5e-3 on a few pairs in a thousand.
+ *   EDM_FP16_TARGETS: 11 significant bits.  Each centred target is first
+ *     multiplied by a power of two that puts its largest magnitude in
+ *     [2^13, 2^14), so no value overflows; rho does not depend on the scale.
+ *     About 8 times more accurate than BF16 for the same bytes. */
 typedef enum edm_precision {
-    EDM_FP32 = 0,         /* targets stored as float32                  */
-    EDM_BF16_TARGETS = 1  /* targets stored as bfloat16 (half the bytes) */
+    EDM_FP32 = 0,          /* targets stored as float32                   */
+    EDM_BF16_TARGETS = 1,  /* targets stored as bfloat16 (half the bytes) */
+    EDM_FP16_TARGETS = 2   /* targets stored as scaled float16 (half the bytes) */
 } edm_precision;
 
 enum {
@@ -94,6 +104,16 @@ const char *edm_last_error(edm_ctx *ctx);
 /* Number of kernels libedm has launched through this context. */
 uint64_t edm_kernel_launches(edm_ctx *ctx);
 
+/* Diagnostics of the exact kNN (no counterpart in the paper).  With the
+ * option "diagnostics" set to 1, every kernel that selects neighbours counts
+ * the query rows (one per row and E) whose FP32 ranking left a candidate
+ * inside the band around the k-th distance, so that the row was resolved in
+ * FP64 (band_rows), and among them the rows with so many tied candidates
+ * that a full FP64 scan was needed (brute_rows).  This call synchronises the
+ * context's stream, returns both counts accumulated since the previous call
+ * and resets them. */
+edm_status edm_fallback_counts(edm_ctx *ctx, uint64_t *band_rows, uint64_t *brute_rows);
+
 /* Measurement aids (no counterpart in the paper).
  * edm_profile_enable(ctx, 1) clears the record and times every kernel this
  * context launches from then on with CUDA events on its stream; 0 stops.
@@ -112,11 +132,13 @@ edm_status edm_probe_smem_bandwidth(edm_ctx *ctx, double ms, double *bytes_per_s
 
 /* Failure-detection check (no counterpart in the paper).  Every wait inside
  * a libedm kernel is bounded: after its limit it records EDM_ERR_TIMEOUT in
- * the context and the kernel runs to its end, so a lost arrival never hangs
- * the GPU.  This call enqueues one thread that waits, with that same bounded
- * wait, on a barrier nothing completes, giving up after `ms` milliseconds
- * (1..10000).  The next edm_ctx_sync then returns EDM_ERR_TIMEOUT (and
- * clears it); the context stays usable. */
+ * the context, sets an abort word of its thread block so that the block's
+ * later waits return at once, and the kernel runs to its end, so a lost
+ * arrival never hangs the GPU.  This call enqueues one thread that waits
+ * twice, with that same bounded wait, on a barrier nothing completes: the
+ * first wait gives up after `ms` milliseconds (1..10000), the second returns
+ * at once.  The next edm_ctx_sync then returns EDM_ERR_TIMEOUT (and clears
+ * it); the context stays usable. */
 edm_status edm_check_wait_timeout(edm_ctx *ctx, int ms);
 
 /* Section 2.1 step 1: time-delay embedding of one series.
@@ -167,9 +189,15 @@ edm_status edm_simplex_optimal_E(edm_ctx *ctx, const float *X, int N, int L,
  * finishing kernel reads, so nothing stale is used, but two calls whose work
  * overlaps on the GPU (different streams, or different host threads) race
  * and both results are then undefined.  Serialise them.
- * Results equal those of edm_simplex_optimal_E on the same inputs.  Errors
- * are returned only as status codes (there is no context to hold a message);
- * launch failures return EDM_ERR_CUDA. */
+ * It runs the same sweep and finishing kernels, with the same split of query
+ * rows into blocks, as edm_simplex_optimal_E, so the results are the same.
+ * Only if that split's partial moments did not fit the array (possible on a
+ * GPU with many more SMs) would it use one block per series; the FP64
+ * summation order then changes, rho_E can differ in the last bits and E*
+ * only at a near-tie.  Errors are returned only as status codes (there is no
+ * context to hold a message): EDM_ERR_CUDA for a launch failure, and also
+ * when a CUDA error was already pending before the call (it is left pending
+ * for its owner). */
 edm_status edm_simplex_optimal_E_noalloc(const float *X, int N, int L, int E_max,
                                          int tau, int Tp_sel, int32_t *E_opt,
                                          float *rho_E, void *cuda_stream);
@@ -188,6 +216,17 @@ edm_status edm_ccm_all(edm_ctx *ctx, const float *X_lib, int N_lib,
                        const int32_t *E_lib, int tau, int Tp,
                        edm_precision prec, float *rho);
 
+/* Row block of one all-to-all CCM problem (section 2.1: libraries are
+ * independent, so the rows of rho can be computed in blocks, e.g. one block
+ * per GPU with the series replicated on every GPU).  X [N][L] float32 holds
+ * the series, which serve both as libraries and as targets; E_lib [N] int32
+ * (device) the E of every series; only the library rows lib_begin ..
+ * lib_end-1 are computed: rho [lib_end-lib_begin][N] float32, row r = library
+ * lib_begin + r.  0 <= lib_begin <= lib_end <= N; an empty block does
+ * nothing.  Otherwise as edm_ccm_all. */
+edm_status edm_ccm_rows(edm_ctx *ctx, const float *X, int N, int L, int lib_begin, int lib_end,
+                        const int32_t *E_lib, int tau, int Tp, edm_precision prec, float *rho);
+
 /* edm_ccm_all that also delivers rho to host memory (no counterpart in the
  * paper).  rho [N_lib][N_tgt] (device) as in edm_ccm_all; rho_host: a
  * page-locked host buffer of the same shape (cudaMallocHost or
@@ -201,6 +240,15 @@ edm_status edm_ccm_all_host(edm_ctx *ctx, const float *X_lib, int N_lib,
                             const float *Y_tgt, int N_tgt, int L,
                             const int32_t *E_lib, int tau, int Tp,
                             edm_precision prec, float *rho, float *rho_host);
+
+/* Stream-ordered upload of N series of L float32 values (no counterpart in
+ * the paper): X_host, page-locked host memory (cudaMallocHost or
+ * cudaHostRegister; other memory returns EDM_ERR_INVALID_ARG), is copied to
+ * the device array X [N][L] on the context's stream, so that a whole CCM
+ * step -- upload, optimal E, tables, lookup, download through
+ * edm_ccm_all_host -- is one ordered sequence of library calls.  The copy is
+ * complete when work queued after it on the context's stream runs. */
+edm_status edm_upload_series(edm_ctx *ctx, const float *X_host, int N, int L, float *X);
 
 /* Pairwise CCM with the embedding dimension chosen per TARGET (section 3.3:
  * targets are grouped by their optimal E, and for each group every library
@@ -296,6 +344,7 @@ edm_status edm_simplex_optimal_E_batched(edm_ctx *ctx, const edm_instance *inst,
  *   "lookup_libs_per_cta"  0..4096 fixed libraries per CTA, 0 = tuned (0)
  *   "table_budget_mb"      >= 16  workspace for neighbour tables (2048)
  *   "autotune_reset"       1      forget the tuned values
+ *   "diagnostics"          0/1    count FP64 band and brute-force rows (0)
  * Returns EDM_ERR_INVALID_ARG for an unknown name or value. */
 edm_status edm_set_option(edm_ctx *ctx, const char *name, long long value);
 

@@ -112,7 +112,7 @@ static int ccm_chunk(edm_ctx *ctx, int N_lib, size_t slot) {
 static size_t ccm_workspace_bytes(edm_ctx *ctx, int N_lib, int N_tgt, int L, int tau, int Tp,
                                   edm_precision prec) {
     const size_t yt_bytes = target_store_bytes(N_tgt, L, prec, lookup_row_words(ctx, L, prec));
-    const size_t mean_bytes = align_up(sizeof(double) * N_tgt, 256);
+    const size_t mean_bytes = align_up(2 * sizeof(double) * N_tgt, 256);
     const size_t sums_bytes = align_up(sizeof(double) * N_tgt * EDM_E_MAX, 256);
     const size_t slot = ccm_slot_bytes(L, tau, Tp);
     if (slot == 0) return yt_bytes + mean_bytes + 2 * sums_bytes;
@@ -137,7 +137,7 @@ static edm_status ccm_one(edm_ctx *ctx, const float *X_lib, long long ld_lib, in
                           int max_block = 0) {
     const int rw = lookup_row_words(ctx, L, prec);
     const size_t yt_bytes = target_store_bytes(N_tgt, L, prec, rw);
-    const size_t mean_bytes = align_up(sizeof(double) * N_tgt, 256);
+    const size_t mean_bytes = align_up(2 * sizeof(double) * N_tgt, 256);
     const size_t sums_bytes = align_up(sizeof(double) * N_tgt * EDM_E_MAX, 256);
     const size_t slot = ccm_slot_bytes(L, tau, Tp);
     if (slot == 0) return set_error(ctx, EDM_ERR_INVALID_ARG, "series too short");
@@ -209,6 +209,8 @@ static edm_ctx *make_sub(edm_ctx *main) {
     sub->num_sms = main->num_sms;
     sub->max_smem_optin = main->max_smem_optin;
     sub->d_flags = main->d_flags;
+    sub->d_stats = main->d_stats;
+    sub->diag = main->diag;
     sub->table_budget = main->table_budget;
     sub->tune = main->tune;
     sub->is_sub = true;
@@ -428,13 +430,14 @@ edm_status edm_create(edm_ctx **out, int device, void *cuda_stream) {
             cudaSuccess ||
         cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
                                device) != cudaSuccess ||
-        cudaMalloc(&ctx->d_flags, sizeof(int)) != cudaSuccess ||
-        cudaMemset(ctx->d_flags, 0, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&ctx->d_flags, 32) != cudaSuccess ||   // flags word, then the two counters
+        cudaMemset(ctx->d_flags, 0, 32) != cudaSuccess) {
         cudaGetLastError();
         if (ctx->d_flags) cudaFree(ctx->d_flags);
         delete ctx;
         return EDM_ERR_CUDA;
     }
+    ctx->d_stats = reinterpret_cast<unsigned long long *>(reinterpret_cast<char *>(ctx->d_flags) + 16);
     *out = ctx;
     return EDM_OK;
 }
@@ -492,6 +495,22 @@ edm_status edm_ctx_sync(edm_ctx *ctx) {
 }
 
 const char *edm_last_error(edm_ctx *ctx) { return ctx ? ctx->last_error : ""; }
+
+edm_status edm_fallback_counts(edm_ctx *ctx, uint64_t *band_rows, uint64_t *brute_rows) {
+    if (!ctx || !band_rows || !brute_rows) return EDM_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    unsigned long long c[2] = {0, 0};
+    edm_status st = cuda_check(ctx, cudaMemcpyAsync(c, ctx->d_stats, sizeof(c),
+                                                    cudaMemcpyDeviceToHost, ctx->stream),
+                               "counter read");
+    if (st == EDM_OK)
+        st = cuda_check(ctx, cudaMemsetAsync(ctx->d_stats, 0, sizeof(c), ctx->stream), "counter reset");
+    if (st == EDM_OK) st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "counter sync");
+    if (st != EDM_OK) return st;
+    *band_rows = c[0];
+    *brute_rows = c[1];
+    return EDM_OK;
+}
 
 edm_status edm_profile_enable(edm_ctx *ctx, int on) {
     if (!ctx) return EDM_ERR_INVALID_ARG;
@@ -579,11 +598,23 @@ edm_status edm_ccm_all(edm_ctx *ctx, const float *X_lib, int N_lib, const float 
                        float *rho) {
     if (!ctx) return EDM_ERR_INVALID_ARG;
     if (!X_lib || !Y_tgt || !E_lib || !rho || N_lib < 1 || N_tgt < 1 || !series_len_ok(L) ||
-        tau < 1 || Tp < 0 || L - Tp < 3 || (prec != EDM_FP32 && prec != EDM_BF16_TARGETS))
+        tau < 1 || Tp < 0 || L - Tp < 3 || !precision_ok(prec))
         return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_all: bad arguments");
     DeviceGuard g(ctx->device);
     return ccm_one(ctx, X_lib, L, N_lib, Y_tgt, L, N_tgt, L, E_lib, 0, tau, Tp, prec, rho, N_tgt,
                    nullptr, nullptr);
+}
+
+edm_status edm_ccm_rows(edm_ctx *ctx, const float *X, int N, int L, int lib_begin, int lib_end,
+                        const int32_t *E_lib, int tau, int Tp, edm_precision prec, float *rho) {
+    if (!ctx) return EDM_ERR_INVALID_ARG;
+    if (!X || !E_lib || !rho || N < 1 || lib_begin < 0 || lib_end > N || lib_begin > lib_end ||
+        !series_len_ok(L) || tau < 1 || Tp < 0 || L - Tp < 3 || !precision_ok(prec))
+        return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_rows: bad arguments");
+    if (lib_begin == lib_end) return EDM_OK;
+    DeviceGuard g(ctx->device);
+    return ccm_one(ctx, X + static_cast<size_t>(lib_begin) * L, L, lib_end - lib_begin, X, L, N, L,
+                   E_lib + lib_begin, 0, tau, Tp, prec, rho, N, nullptr, nullptr);
 }
 
 edm_status edm_ccm_all_host(edm_ctx *ctx, const float *X_lib, int N_lib, const float *Y_tgt,
@@ -592,7 +623,7 @@ edm_status edm_ccm_all_host(edm_ctx *ctx, const float *X_lib, int N_lib, const f
     if (!ctx) return EDM_ERR_INVALID_ARG;
     if (!X_lib || !Y_tgt || !E_lib || !rho || !rho_host || N_lib < 1 || N_tgt < 1 ||
         !series_len_ok(L) || tau < 1 || Tp < 0 || L - Tp < 3 ||
-        (prec != EDM_FP32 && prec != EDM_BF16_TARGETS))
+        !precision_ok(prec))
         return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_all_host: bad arguments");
     DeviceGuard g(ctx->device);
     cudaPointerAttributes attr;
@@ -611,12 +642,29 @@ edm_status edm_ccm_all_host(edm_ctx *ctx, const float *X_lib, int N_lib, const f
                    nullptr, nullptr, rho_host, block);
 }
 
+edm_status edm_upload_series(edm_ctx *ctx, const float *X_host, int N, int L, float *X) {
+    if (!ctx) return EDM_ERR_INVALID_ARG;
+    if (!X_host || !X || N < 1 || L < 1)
+        return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_upload_series: bad arguments");
+    DeviceGuard g(ctx->device);
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, X_host) != cudaSuccess ||
+        attr.type != cudaMemoryTypeHost) {
+        cudaGetLastError();
+        return set_error(ctx, EDM_ERR_INVALID_ARG,
+                         "edm_upload_series: X_host must be page-locked host memory");
+    }
+    return cuda_check(ctx, cudaMemcpyAsync(X, X_host, sizeof(float) * static_cast<size_t>(N) * L,
+                                           cudaMemcpyHostToDevice, ctx->stream),
+                      "series upload");
+}
+
 edm_status edm_ccm_all_target_E(edm_ctx *ctx, const float *X_lib, int N_lib, const float *Y_tgt,
                                 int N_tgt, int L, const int32_t *E_tgt, int tau, int Tp,
                                 edm_precision prec, float *rho) {
     if (!ctx) return EDM_ERR_INVALID_ARG;
     if (!X_lib || !Y_tgt || !E_tgt || !rho || N_lib < 1 || N_tgt < 1 || !series_len_ok(L) ||
-        tau < 1 || Tp < 0 || L - Tp < 3 || (prec != EDM_FP32 && prec != EDM_BF16_TARGETS))
+        tau < 1 || Tp < 0 || L - Tp < 3 || !precision_ok(prec))
         return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_all_target_E: bad arguments");
     DeviceGuard g(ctx->device);
     // the targets' E values decide which tables exist: read them (one sync)
@@ -667,7 +715,7 @@ edm_status edm_ccm_window(edm_ctx *ctx, const float *X, int N, int ld, int offse
     if (!ctx) return EDM_ERR_INVALID_ARG;
     if (!X || !E_lib || !rho || N < 1 || offset < 0 || !series_len_ok(L_win) ||
         static_cast<long long>(offset) + L_win > ld || tau < 1 || Tp < 0 || L_win - Tp < 3 ||
-        (prec != EDM_FP32 && prec != EDM_BF16_TARGETS))
+        !precision_ok(prec))
         return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_window: bad arguments");
     DeviceGuard g(ctx->device);
     const float *base = X + offset;
@@ -711,7 +759,7 @@ edm_status edm_ccm_windows(edm_ctx *ctx, const float *X, int N, int ld, const in
                            edm_precision prec, float *rho) {
     if (!ctx) return EDM_ERR_INVALID_ARG;
     if (!X || !offsets || !E_lib || !rho || N < 1 || n_windows < 1 || !series_len_ok(L_win) ||
-        tau < 1 || Tp < 0 || L_win - Tp < 3 || (prec != EDM_FP32 && prec != EDM_BF16_TARGETS))
+        tau < 1 || Tp < 0 || L_win - Tp < 3 || !precision_ok(prec))
         return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_windows: bad arguments");
     for (int w = 0; w < n_windows; ++w)
         if (offsets[w] < 0 || static_cast<long long>(offsets[w]) + L_win > ld)
@@ -734,7 +782,7 @@ static bool instance_ok(const edm_instance &p) {
 edm_status edm_ccm_batched(edm_ctx *ctx, const edm_instance *inst, int n_inst,
                            edm_precision prec) {
     if (!ctx) return EDM_ERR_INVALID_ARG;
-    if (!inst || n_inst < 0 || (prec != EDM_FP32 && prec != EDM_BF16_TARGETS))
+    if (!inst || n_inst < 0 || !precision_ok(prec))
         return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_ccm_batched: bad arguments");
     for (int i = 0; i < n_inst; ++i)
         if (!instance_ok(inst[i]) || !inst[i].rho)
@@ -825,6 +873,8 @@ edm_status edm_set_option(edm_ctx *ctx, const char *name, long long value) {
         ctx->table_budget = static_cast<size_t>(value) << 20;
     } else if (!strcmp(name, "autotune_reset") && value == 1) {
         ctx->tune->clear();
+    } else if (!strcmp(name, "diagnostics") && (value == 0 || value == 1)) {
+        ctx->diag = value != 0;
     } else {
         return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_set_option: bad option %s=%lld", name,
                          value);

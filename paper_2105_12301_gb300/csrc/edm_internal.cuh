@@ -24,6 +24,8 @@ struct edm_ctx {
     void *ws;                  // workspace (neighbour tables, transposed targets, partials)
     size_t ws_bytes;
     int *d_flags;              // device-side error flags (EDMF_*)
+    unsigned long long *d_stats;  // [2]: rows resolved in the FP64 band, by FP64 brute force
+    bool diag = false;         // count those rows (edm_set_option "diagnostics")
     uint64_t launches;         // kernels launched through this context
     size_t table_budget;       // bytes of workspace a chunk of neighbour tables may use
     char last_error[256];
@@ -77,6 +79,8 @@ void before_launch(edm_ctx *ctx);
 edm_status after_launch(edm_ctx *ctx, const char *kernel);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+// The fallback counters a kernel adds to, or NULL when diagnostics are off.
+inline unsigned long long *diag_stats(edm_ctx *ctx) { return ctx->diag ? ctx->d_stats : nullptr; }
 
 // Layout of a CCM neighbour table (k = E+1 neighbours, n rows).  Rows are
 // stored in pairs (2p, 2p+1).  A row's logical words are its first k-1
@@ -106,9 +110,12 @@ __host__ __device__ inline bool ccm_E_valid(int E, int L, int tau, int Tp) {
 }
 
 constexpr int LK_GROUP_FP32 = 4;
-constexpr int LK_GROUP_BF16 = 2;
+constexpr int LK_GROUP_16 = 2;   // 16-bit targets: two per lane, so fewer libraries
 inline int lookup_group(edm_precision prec) {
-    return prec == EDM_BF16_TARGETS ? LK_GROUP_BF16 : LK_GROUP_FP32;
+    return prec != EDM_FP32 ? LK_GROUP_16 : LK_GROUP_FP32;
+}
+inline bool precision_ok(edm_precision prec) {
+    return prec == EDM_FP32 || prec == EDM_BF16_TARGETS || prec == EDM_FP16_TARGETS;
 }
 struct CcmGroups {
     int32_t *E;      // [ngroups_max] E of the members (0: invalid E)
@@ -144,7 +151,8 @@ edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max,
                           int Tp_sel, int32_t *E_opt, float *rho_E);
 // Transposed, centred target tiles plus, per E = 1..EDM_E_MAX, the FP64 sums
 // of the stored values and of their squares over the observation window of
-// E (times (E-1)tau+Tp .. L-1): ysum / yysum [EDM_E_MAX][N_tgt].
+// E (times (E-1)tau+Tp .. L-1): ysum / yysum [EDM_E_MAX][N_tgt].  mean_ws
+// holds 2 * N_tgt doubles (each target's mean, then its FP16 scale).
 // Y: target series with row stride ld (>= L) floats; target r of the store is
 // series rows[r] (series r when rows is NULL).  rw: 32-bit words per tile
 // row (lookup_row_words).
@@ -276,17 +284,24 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
 
 // Wait for the phase with the given parity to complete, for at most
 // limit_ns nanoseconds (two seconds by default).  On timeout the context's
-// error flag is raised and false is returned; the caller carries on (its
-// data is then garbage) so that every thread still reaches every later
-// barrier and the kernel always ends.
+// error flag is raised, the CTA's abort word (when given) is set and false
+// is returned; the caller carries on without the data it waited for, so that
+// every thread still reaches every later barrier and the kernel always ends.
+// Once the abort word is set, every later wait of the CTA that passes it
+// returns false at once instead of spinning for its own limit, so a CTA
+// whose pipeline broke ends within about one limit.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *flags,
+                                                  volatile int *abort,
                                                   uint64_t limit_ns = 2000000000ull) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (abort && *abort) return false;
     const uint64_t t0 = global_timer_ns();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (abort && *abort) return false;
         if (global_timer_ns() - t0 > limit_ns) {
             set_flag(flags, EDMF_TIMEOUT);
+            if (abort) *abort = 1;
             return false;
         }
     }

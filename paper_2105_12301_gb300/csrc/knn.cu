@@ -75,7 +75,8 @@ static int rows_per_cta(edm_ctx *ctx, int N, int n) {
 template <int E, bool SMEM>
 __global__ void __launch_bounds__(KNN_WARPS * 32)
     knn_out_kernel(const float *__restrict__ X, int L, int tau, int Tp, int K, int RB,
-                   int32_t *__restrict__ idx, float *__restrict__ dist) {
+                   int32_t *__restrict__ idx, float *__restrict__ dist,
+                   unsigned long long *stats) {
     extern __shared__ __align__(16) uint8_t smem[];
     WarpScratch *wsa = reinterpret_cast<WarpScratch *>(smem);
     float *xs_s = reinterpret_cast<float *>(smem + KNN_WARPS * sizeof(WarpScratch));
@@ -85,16 +86,18 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
     const int r0 = blockIdx.y * RB, r1 = min(n, r0 + RB);
     const int warp = threadIdx.x >> 5, lane = lane_id();
     WarpScratch *ws = wsa + warp;
+    FallbackCount fc;
     for (int i = r0 + warp; i < r1; i += KNN_WARPS) {
         int u = 0;
         float d = 0.f;
-        knn_row<E, KNN_ORDERED>(xs, lo + i, lo, hi, tau, K, ws, &u, &d);
+        fc.add(knn_row<E, KNN_ORDERED>(xs, lo + i, lo, hi, tau, K, ws, &u, &d));
         const size_t o = (static_cast<size_t>(series) * n + i) * K;
         if (lane < K) {
             idx[o + lane] = u;
             if (dist) dist[o + lane] = d;
         }
     }
+    fc.flush(stats);
 }
 
 // edm_knn for series longer than 2,048 points: chunked candidates held in
@@ -102,7 +105,8 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
 template <bool SMEM>
 __global__ void __launch_bounds__(KNN_WARPS * 32)
     knn_out_long_kernel(const float *__restrict__ X, int L, int E, int tau, int Tp, int K, int RB,
-                        int32_t *__restrict__ idx, float *__restrict__ dist);
+                        int32_t *__restrict__ idx, float *__restrict__ dist,
+                        unsigned long long *stats);
 
 template <int E>
 static edm_status launch_knn_E(edm_ctx *ctx, const float *X, int N, int L, int tau, int Tp, int K,
@@ -116,12 +120,14 @@ static edm_status launch_knn_E(edm_ctx *ctx, const float *X, int N, int L, int t
         auto kern = knn_out_kernel<E, true>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         before_launch(ctx);
-        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, L, tau, Tp, K, RB, idx, dist);
+        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, L, tau, Tp, K, RB, idx, dist,
+                                                          diag_stats(ctx));
     } else {
         auto kern = knn_out_kernel<E, false>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         before_launch(ctx);
-        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, L, tau, Tp, K, RB, idx, dist);
+        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, L, tau, Tp, K, RB, idx, dist,
+                                                          diag_stats(ctx));
     }
     return after_launch(ctx, "knn_out_kernel");
 }
@@ -138,7 +144,8 @@ edm_status launch_knn(edm_ctx *ctx, const float *X, int N, int L, int E, int tau
         auto kern = smem_series ? knn_out_long_kernel<true> : knn_out_long_kernel<false>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         before_launch(ctx);
-        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, L, E, tau, Tp, k, RB, idx, dist);
+        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, L, E, tau, Tp, k, RB, idx, dist,
+                                                          diag_stats(ctx));
         return after_launch(ctx, "knn_out_kernel");
     }
     switch (E) {
@@ -211,7 +218,8 @@ __device__ __forceinline__ bool table_slot(const CcmGroups &g, uint8_t *tables, 
 template <int CH, bool HEAD1>
 __global__ void __launch_bounds__(KNN_WARPS * 32)
     ccm_table_regs_kernel(const float *__restrict__ X, long long ld, int L, int tau, int Tp,
-                          int RB, const CcmGroups g, uint8_t *__restrict__ tables) {
+                          int RB, const CcmGroups g, uint8_t *__restrict__ tables,
+                          unsigned long long *stats) {
     extern __shared__ __align__(16) uint8_t smem[];
     WarpScratch *wsa = reinterpret_cast<WarpScratch *>(smem);
     float *xs = reinterpret_cast<float *>(smem + KNN_WARPS * sizeof(WarpScratch));
@@ -227,6 +235,8 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = lane_id();
     WarpScratch *ws = wsa + warp;
+    const unsigned keep = bitonic_keep_min_bits();
+    FallbackCount fc;
     for (int i = r0 + warp; i < r1; i += KNN_WARPS) {
         const int t = lo + i;
         float s[CH];
@@ -248,10 +258,11 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
         }
         int u = 0;
         float d = 0.f;
-        select_set_regs<CH>(s, xs, t, lo, hi, E, tau, K, ws, u, d);
+        fc.add(select_set_regs<CH>(s, xs, t, lo, hi, E, tau, K, ws, u, d, keep));
         const float w = simplex_weight(d, K);
         write_table_row(ts.base, ts.pair_stride, i, n, K, L, Tp, u, w);
     }
+    fc.flush(stats);
 }
 
 // ------------------------------------------- tables of long series (> 2,048)
@@ -267,8 +278,8 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
 //     FP64 square root rounded to float.
 // On return lane r < K holds the r-th neighbour and its distance.
 template <int MODE>
-__device__ void knn_row_chunked(const float *xs, int L, int t, int lo, int hi, int E, int tau,
-                                int K, TableLongScratch *sc, int &u_out, float &d_out) {
+__device__ int knn_row_chunked(const float *xs, int L, int t, int lo, int hi, int E, int tau,
+                               int K, TableLongScratch *sc, int &u_out, float &d_out) {
     const int lane = lane_id();
     WarpScratch *ws = &sc->ws;
     uint64_t *list = sc->list;
@@ -342,6 +353,7 @@ __device__ void knn_row_chunked(const float *xs, int L, int t, int lo, int hi, i
         for (int e = lane; e < have; e += 32) list[e] = ws->sel[e];
         __syncwarp();
     }
+    int flags = 0;
     if (!deg) {
         const float edge = band_edge(key_s(list[K - 1]), E);
         if (MODE == KNN_SET && (R <= K || key_s(list[K]) > edge)) {
@@ -350,7 +362,7 @@ __device__ void knn_row_chunked(const float *xs, int L, int t, int lo, int hi, i
                 d_out = sqrtf(key_s(list[lane]));
             }
             __syncwarp();
-            return;
+            return 0;
         }
         if (MODE == KNN_ORDERED && (R == nc || key_s(list[R - 1]) > edge)) {
             // the R collected keys cover the band: rank them in FP64
@@ -376,7 +388,7 @@ __device__ void knn_row_chunked(const float *xs, int L, int t, int lo, int hi, i
                 d_out = __double2float_rn(__dsqrt_rn(ws->sel_s64[lane]));
             }
             __syncwarp();
-            return;
+            return 0;
         }
         // resolve the band in FP64: every candidate with s32 <= edge
         if (lane == 0) ws->count = 0;
@@ -396,24 +408,30 @@ __device__ void knn_row_chunked(const float *xs, int L, int t, int lo, int hi, i
         __syncwarp();
         const int c = ws->count;
         __syncwarp();
-        if (c <= KNN_CAP)
+        flags = KNN_USED_BAND;
+        if (c <= KNN_CAP) {
             rank_band_fp64(xs, t, E, tau, ws, c, K);
-        else
+        } else {
             brute_fp64(xs, t, lo, hi, E, tau, ws, K);
+            flags |= KNN_USED_BRUTE;
+        }
     } else {
         brute_fp64(xs, t, lo, hi, E, tau, ws, K);
+        flags = KNN_USED_BAND | KNN_USED_BRUTE;
     }
     if (lane < K) {
         u_out = ws->sel_u[lane];
         d_out = __double2float_rn(__dsqrt_rn(ws->sel_s64[lane]));
     }
     __syncwarp();
+    return flags;
 }
 
 template <bool SMEM>
 __global__ void __launch_bounds__(KNN_WARPS * 32)
     ccm_table_long_kernel(const float *__restrict__ X, long long ld, int L, int tau, int Tp,
-                          int RB, const CcmGroups g, uint8_t *__restrict__ tables) {
+                          int RB, const CcmGroups g, uint8_t *__restrict__ tables,
+                          unsigned long long *stats) {
     extern __shared__ __align__(16) uint8_t smem[];
     TableLongScratch *sca = reinterpret_cast<TableLongScratch *>(smem);
     float *xs_s = reinterpret_cast<float *>(smem + KNN_WARPS * sizeof(TableLongScratch));
@@ -426,19 +444,22 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
     const float *xs = stage_series<SMEM>(X + static_cast<size_t>(ts.lib) * ld, L, xs_s);
     const int warp = threadIdx.x >> 5;
     TableLongScratch *sc = sca + warp;
+    FallbackCount fc;
     for (int i = r0 + warp; i < r1; i += KNN_WARPS) {
         int u = 0;
         float d = 0.f;
-        knn_row_chunked<KNN_SET>(xs, L, lo + i, lo, hi, E, tau, E + 1, sc, u, d);
+        fc.add(knn_row_chunked<KNN_SET>(xs, L, lo + i, lo, hi, E, tau, E + 1, sc, u, d));
         const float w = simplex_weight(d, E + 1);
         write_table_row(ts.base, ts.pair_stride, i, n, E + 1, L, Tp, u, w);
     }
+    fc.flush(stats);
 }
 
 template <bool SMEM>
 __global__ void __launch_bounds__(KNN_WARPS * 32)
     knn_out_long_kernel(const float *__restrict__ X, int L, int E, int tau, int Tp, int K, int RB,
-                        int32_t *__restrict__ idx, float *__restrict__ dist) {
+                        int32_t *__restrict__ idx, float *__restrict__ dist,
+                        unsigned long long *stats) {
     extern __shared__ __align__(16) uint8_t smem[];
     TableLongScratch *sca = reinterpret_cast<TableLongScratch *>(smem);
     float *xs_s = reinterpret_cast<float *>(smem + KNN_WARPS * sizeof(TableLongScratch));
@@ -448,16 +469,18 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
     const int r0 = blockIdx.y * RB, r1 = min(n, r0 + RB);
     const int warp = threadIdx.x >> 5, lane = lane_id();
     TableLongScratch *sc = sca + warp;
+    FallbackCount fc;
     for (int i = r0 + warp; i < r1; i += KNN_WARPS) {
         int u = 0;
         float d = 0.f;
-        knn_row_chunked<KNN_ORDERED>(xs, L, lo + i, lo, hi, E, tau, K, sc, u, d);
+        fc.add(knn_row_chunked<KNN_ORDERED>(xs, L, lo + i, lo, hi, E, tau, K, sc, u, d));
         const size_t o = (static_cast<size_t>(series) * n + i) * K;
         if (lane < K) {
             idx[o + lane] = u;
             if (dist) dist[o + lane] = d;
         }
     }
+    fc.flush(stats);
 }
 
 size_t ccm_slot_bytes(int L, int tau, int Tp) {
@@ -482,8 +505,8 @@ edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, long long ld, int nli
         for (int c : CHs)
             if (c >= ch) { CH = c; break; }
         const bool head1 = (EDM_E_MAX - 1) * tau < 32;
-        void (*kern)(const float *, long long, int, int, int, int, const CcmGroups, uint8_t *) =
-            nullptr;
+        void (*kern)(const float *, long long, int, int, int, int, const CcmGroups, uint8_t *,
+                     unsigned long long *) = nullptr;
         switch (CH) {
         case 8: kern = head1 ? ccm_table_regs_kernel<8, true> : ccm_table_regs_kernel<8, false>; break;
         case 16: kern = head1 ? ccm_table_regs_kernel<16, true> : ccm_table_regs_kernel<16, false>; break;
@@ -495,7 +518,8 @@ edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, long long ld, int nli
         const size_t smem = KNN_WARPS * sizeof(WarpScratch) + sizeof(float) * 32 * CH;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         before_launch(ctx);
-        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, L, tau, Tp, RB, g, tables);
+        kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, L, tau, Tp, RB, g, tables,
+                                                          diag_stats(ctx));
         return after_launch(ctx, "ccm_table_kernel");
     }
     // longer series: chunks of 1,024 candidates against a running list
@@ -505,7 +529,8 @@ edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, long long ld, int nli
     auto kern = smem_series ? ccm_table_long_kernel<true> : ccm_table_long_kernel<false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     before_launch(ctx);
-    kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, L, tau, Tp, RB, g, tables);
+    kern<<<grid, KNN_WARPS * 32, smem, ctx->stream>>>(X, ld, L, tau, Tp, RB, g, tables,
+                                                      diag_stats(ctx));
     return after_launch(ctx, "ccm_table_kernel");
 }
 

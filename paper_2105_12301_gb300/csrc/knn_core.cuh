@@ -29,12 +29,21 @@ namespace edm {
 
 constexpr int KNN_CAP = 128;     // per-warp candidate buffer
 constexpr int KNN_MARGIN = 8;    // extra FP32 candidates re-ranked in FP64
+constexpr int KNN_CELLS = 64;    // per-warp buffer of 4-slot cells (select_set_regs)
 
+// The cell buffer shares memory with the FP64 band buffers: cells are turned
+// into keys before any band is resolved.
 struct alignas(16) WarpScratch {
     uint64_t key[KNN_CAP];   // collected FP32 keys
-    double s64[KNN_CAP];     // their FP64 squared distances (band fallback)
+    union {
+        double s64[KNN_CAP];        // FP64 squared distances of the keys (band fallback)
+        float4 cell_v[KNN_CELLS];   // the four values of a collected cell
+    };
     uint64_t sel[32];        // the R smallest collected keys, ascending
-    double sel_s64[32];      // exact ranking: FP64 distances by final rank
+    union {
+        double sel_s64[32];         // exact ranking: FP64 distances by final rank
+        int cell_u[KNN_CELLS];      // time index of the first value of a cell
+    };
     int sel_u[32];
     int count;
     int pad;
@@ -309,19 +318,37 @@ __device__ int knn_row(const float *xs, int t, int lo, int hi, int tau, int K, W
 
 #define EDM_INF __int_as_float(0x7f800000)
 
-// Ascending bitonic sort of one float per lane; value at position r.
-__device__ __forceinline__ float warp_sorted_at_f(float v, int r) {
+// Bit i of the result is set when this lane keeps the smaller value at
+// compare-exchange stage i of the ascending 32-lane bitonic network (stages
+// in the order of warp_sorted_at_f).  A per-lane constant: computed once.
+__device__ __forceinline__ unsigned bitonic_keep_min_bits() {
     const int lane = lane_id();
+    unsigned bits = 0;
+    int st = 0;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1, ++st)
+            if (((lane & k) == 0) == ((lane & j) == 0)) bits |= 1u << st;
+    return bits;
+}
+
+// Ascending bitonic sort of one float per lane; value at position r.  keep
+// is bitonic_keep_min_bits() of this lane.
+__device__ __forceinline__ float warp_sorted_at_f(float v, int r, unsigned keep) {
+    int st = 0;
 #pragma unroll
     for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1, ++st) {
             const float o = __shfl_xor_sync(FULL, v, j);
-            const bool up = (lane & k) == 0, lower = (lane & j) == 0;
-            v = (lower == up) ? fminf(v, o) : fmaxf(v, o);
+            v = (keep >> st) & 1u ? fminf(v, o) : fmaxf(v, o);
         }
     }
     return __shfl_sync(FULL, v, r);
+}
+__device__ __forceinline__ float warp_sorted_at_f(float v, int r) {
+    return warp_sorted_at_f(v, r, bitonic_keep_min_bits());
 }
 
 // Compact the keys (s[j], u0+lane+32j) with s[j] <= bound (and finite, i.e. a
@@ -381,6 +408,70 @@ __device__ __forceinline__ int compact_le_groups(const float (&s)[CH], const flo
     return base;
 }
 
+// Compact the 4-slot cells (lane, group g) whose minimum gm[g] is at or below
+// a FINITE bound into ws->cell_v / ws->cell_u: the lane writes the cell's four
+// values and the time index of its first slot, u0 + lane + 128 g.  Visits
+// only the groups in which some lane holds such a cell.  Returns the number
+// of cells (only the first KNN_CELLS are stored).  On this data nearly every
+// value at or below the lane-minimum bound is the minimum of its cell, so a
+// cell is written with one 16-byte store where compact_le_groups spends a
+// ballot on each of its four slots.
+template <int CH>
+__device__ __forceinline__ int compact_cells(const float (&s)[CH], const float (&gm)[CH / 4],
+                                             float bound, WarpScratch *ws, int u0 = 0) {
+    const int lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    int base = 0;
+#pragma unroll
+    for (int g = 0; g < CH / 4; ++g) {
+        const bool p = gm[g] <= bound;
+        const unsigned b = __ballot_sync(FULL, p);
+        if (b) {
+            if (p) {
+                const int pos = base + __popc(b & lt);
+                if (pos < KNN_CELLS) {
+                    ws->cell_v[pos] = make_float4(s[4 * g], s[4 * g + 1], s[4 * g + 2], s[4 * g + 3]);
+                    ws->cell_u[pos] = u0 + lane + 128 * g;
+                }
+            }
+            base += __popc(b);
+        }
+    }
+    __syncwarp();
+    return base;
+}
+
+// The keys of the values at or below `bound` in the first M (<= KNN_CELLS)
+// cells, into ws->key; returns how many there are (at most 4 M; only the
+// first KNN_CAP are stored).  Value i of a cell is time u0 + 32 i.
+__device__ __forceinline__ int cells_to_keys(WarpScratch *ws, int M, float bound) {
+    const int lane = lane_id();
+    const unsigned lt = (1u << lane) - 1u;
+    int base = 0;
+    for (int e0 = 0; e0 < M; e0 += WARP) {
+        const int e = e0 + lane;
+        float4 v = make_float4(EDM_INF, EDM_INF, EDM_INF, EDM_INF);
+        int u0 = 0;
+        if (e < M) {
+            v = ws->cell_v[e];
+            u0 = ws->cell_u[e];
+        }
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const bool p = vv[i] <= bound;
+            const unsigned b = __ballot_sync(FULL, p);
+            if (p) {
+                const int pos = base + __popc(b & lt);
+                if (pos < KNN_CAP) ws->key[pos] = mk_key(vv[i], u0 + 32 * i);
+            }
+            base += __popc(b);
+        }
+    }
+    __syncwarp();
+    return base;
+}
+
 // Minima of the 4-slot groups of a register array.
 template <int CH>
 __device__ __forceinline__ void group_minima(const float (&s)[CH], float (&gm)[CH / 4]) {
@@ -432,13 +523,16 @@ __device__ __forceinline__ float shrink_bound(const float (&s)[CH], float hi, in
 // from the FP32 squared distances held in registers: s[j] is the distance to
 // the candidate u = lane + 32 j, +inf when u is not a candidate.  Steps as in
 // knn_row's KNN_SET mode: lane minima, the (K+1)-th smallest of them as a
-// bound, ballot-compaction of the values at or below it, exact ranking of the
-// collected keys, then the band check (resolved in FP64 when it fails).  On
-// return lane r < K holds the r-th neighbour and its distance.
+// bound, compaction of the values at or below it (through 4-slot cells),
+// exact ranking of the collected keys, then the band check (resolved in FP64
+// when it fails).  On return lane r < K holds the r-th neighbour and its
+// distance.  keep: bitonic_keep_min_bits() of this lane.  Returns KNN_USED_*
+// flags (the same in every lane).
 template <int CH>
-__device__ __forceinline__ void select_set_regs(const float (&s)[CH], const float *xs, int t,
-                                                int lo, int hi, int E, int tau, int K,
-                                                WarpScratch *ws, int &u_out, float &d_out) {
+__device__ __forceinline__ int select_set_regs(const float (&s)[CH], const float *xs, int t,
+                                               int lo, int hi, int E, int tau, int K,
+                                               WarpScratch *ws, int &u_out, float &d_out,
+                                               unsigned keep) {
     constexpr int NG = CH / 4;
     const int lane = lane_id();
     const int nc = hi - lo;
@@ -449,15 +543,21 @@ __device__ __forceinline__ void select_set_regs(const float (&s)[CH], const floa
     float lmin = EDM_INF;
 #pragma unroll
     for (int g = 0; g < NG; ++g) lmin = fminf(lmin, gm[g]);
-    const float theta = warp_sorted_at_f(lmin, R - 1);
+    const float theta = warp_sorted_at_f(lmin, R - 1, keep);
     // a finite theta excludes the +inf non-candidates by itself
-    int c = theta == EDM_INF ? compact_le<CH>(s, theta, ws)
-                             : compact_le_groups<CH>(s, gm, theta, ws);
+    int c;
+    if (theta == EDM_INF) {
+        c = compact_le<CH>(s, theta, ws);
+    } else {
+        const int M = compact_cells<CH>(s, gm, theta, ws);
+        c = M <= KNN_CELLS ? cells_to_keys(ws, M, theta) : compact_le_groups<CH>(s, gm, theta, ws);
+    }
     if (c > KNN_CAP) {
         // a loose threshold: shrink it so that the values under it fit
         const float b = shrink_bound<CH>(s, theta, c, R, KNN_CAP, [](float) { return 0; });
         if (b >= 0.f) c = compact_le_groups<CH>(s, gm, b, ws);
     }
+    int flags = 0;
     if (c <= KNN_CAP) {
         rank_keys(ws, c, R);
         const float edge = band_edge(key_s(ws->sel[K - 1]), E);
@@ -468,24 +568,46 @@ __device__ __forceinline__ void select_set_regs(const float (&s)[CH], const floa
                 d_out = sqrtf(key_s(k));
             }
             __syncwarp();
-            return;
+            return 0;
         }
         // resolve the band in FP64
+        flags = KNN_USED_BAND;
         c = compact_le<CH>(s, edge, ws);
-        if (c <= KNN_CAP)
+        if (c <= KNN_CAP) {
             rank_band_fp64(xs, t, E, tau, ws, c, K);
-        else
+        } else {
             brute_fp64(xs, t, lo, hi, E, tau, ws, K);
+            flags |= KNN_USED_BRUTE;
+        }
     } else {
         // more than KNN_CAP values tie (long runs of repeats)
         brute_fp64(xs, t, lo, hi, E, tau, ws, K);
+        flags = KNN_USED_BAND | KNN_USED_BRUTE;
     }
     if (lane < K) {
         u_out = ws->sel_u[lane];
         d_out = __double2float_rn(__dsqrt_rn(ws->sel_s64[lane]));
     }
     __syncwarp();
+    return flags;
 }
+
+// Per-warp counts of the rows whose neighbour set needed the FP64 band
+// (KNN_USED_BAND) and an FP64 brute-force scan (KNN_USED_BRUTE); lane 0 adds
+// them to stats[0] / stats[1] once per warp when diagnostics are on.
+struct FallbackCount {
+    unsigned band = 0, brute = 0;
+    __device__ __forceinline__ void add(int flags) {
+        band += (flags & KNN_USED_BAND) ? 1u : 0u;
+        brute += (flags & KNN_USED_BRUTE) ? 1u : 0u;
+    }
+    __device__ __forceinline__ void flush(unsigned long long *stats) const {
+        if (stats && lane_id() == 0 && (band | brute)) {
+            if (band) atomicAdd(stats, static_cast<unsigned long long>(band));
+            if (brute) atomicAdd(stats + 1, static_cast<unsigned long long>(brute));
+        }
+    }
+};
 
 // Simplex weights of the K neighbours held one per lane (lane r < K holds
 // distance d of rank r; lane 0 the nearest): w = exp(-d/d1) normalised, or

@@ -2,7 +2,8 @@
 // steps 3-4, Algorithm 3 and the closing paragraph of section 3.3).
 //
 // Targets are first stored transposed and centred, in tiles of 32 (FP32) or
-// 64 (BF16) targets: Yt[tile][u][lane], one 128-byte row per time u.  One
+// 64 (BF16 or FP16, two per 32-bit word) targets: Yt[tile][u][lane], one
+// 128-byte row per time u.  One
 // CTA owns one target tile (staged in shared memory by a bulk TMA copy) and
 // a block of library groups (libraries of equal E, see CcmGroups).  A
 // producer warp streams the groups' interleaved neighbour tables through a
@@ -17,22 +18,35 @@
 // observation in FP32, per member.  The target's own sums over the
 // observation window are precomputed in FP64 per (target, E).  At the end of
 // a group, consumer warp w+8 hands its partial moments to warp w, which adds
-// them to its own and passes the sum on; a finisher warp adds those eight
+// them to its own in FP32 and passes the sum on; a finisher warp adds those
+// eight with compensated (TwoSum) FP32 arithmetic, finishes the sums in FP64
 // and forms rho in FP64 (a fixed summation order, handed over through
 // mbarriers).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "edm_internal.cuh"
 
 namespace edm {
 
+// Target storage formats (the edm_precision values): FP32, or two 16-bit
+// values per 32-bit tile word (BF16, or FP16 scaled per target by a power of
+// two).  unpack_target gives value c (0: low half, 1: high half) of a word.
+template <int FMT>
+__device__ __forceinline__ float unpack_target(uint32_t v, int c) {
+    if (FMT == EDM_FP32) return __uint_as_float(v);
+    if (FMT == EDM_BF16_TARGETS) return __uint_as_float(c == 0 ? (v << 16) : (v & 0xffff0000u));
+    return __half2float(__ushort_as_half(static_cast<unsigned short>(c == 0 ? (v & 0xffffu) : (v >> 16))));
+}
+
 // Warp roles of the lookup CTA; G libraries per group, NM FP32 moments per
 // lane and library (3 per target: sum of the prediction, of its square and
 // of its product with the observation).
-template <bool BF16> struct LkCfg {
+template <int FMT> struct LkCfg {
+    static constexpr bool PK = FMT != EDM_FP32;    // two targets per lane
     static constexpr int NC = 16;                  // consumer warps
-    static constexpr int G = BF16 ? LK_GROUP_BF16 : LK_GROUP_FP32;
-    static constexpr int NM = BF16 ? 6 : 3;
+    static constexpr int G = PK ? LK_GROUP_16 : LK_GROUP_FP32;
+    static constexpr int NM = PK ? 6 : 3;
     static constexpr int PRODUCER = NC;            // warp issuing the bulk copies
     static constexpr int FINISHER = NC + 1;        // warp turning moments into rho
     static constexpr int THREADS = (NC + 2) * 32;
@@ -48,39 +62,60 @@ __device__ __forceinline__ size_t target_row(const int32_t *rows, int r) {
     return static_cast<size_t>(rows ? rows[r] : r);
 }
 
+// mean[r]: the FP64 mean of stored target r; scale[r]: the power of two
+// 2^(13 - floor(log2 B)), B = max|y| + |mean| >= max|y - mean|, so that the
+// centred, scaled values of an FP16 store lie below 2^14 in magnitude with
+// the largest of them at full FP16 precision (1 when B is 0 or not finite).
+// Pearson's rho does not change when a target is scaled, so the scale is
+// never undone.
 __global__ void target_mean_kernel(const float *__restrict__ Y, long long ld,
                                    const int32_t *__restrict__ rows, int N, int L,
-                                   double *__restrict__ mean) {
+                                   double *__restrict__ mean, double *__restrict__ scale) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = lane_id();
     if (warp >= N) return;
     const float *y = Y + target_row(rows, warp) * ld;
     double s = 0.0;
-    for (int i = lane; i < L; i += 32) s += static_cast<double>(y[i]);
+    float amax = 0.f;
+    for (int i = lane; i < L; i += 32) {
+        s += static_cast<double>(y[i]);
+        amax = fmaxf(amax, fabsf(y[i]));
+    }
     s = warp_sum_d(s);
-    if (lane == 0) mean[warp] = s / L;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(FULL, amax, o));
+    if (lane == 0) {
+        const double mu = s / L;
+        mean[warp] = mu;
+        const double B = static_cast<double>(amax) + fabs(mu);
+        scale[warp] = (B > 0.0 && isfinite(B)) ? ldexp(1.0, 13 - ilogb(B)) : 1.0;
+    }
 }
 
 // A tile row holds RW 32-bit words: RW = 32 (128-byte rows) normally, 16
 // (64-byte rows) when a 32-word tile of the series length does not fit
 // shared memory but a 16-word one does.  FP32: Yt[tile][u][RW] = Y[RW tile +
-// w][u] - mean; BF16: word w holds targets 2w (low half) and 2w+1 (high
-// half), each rounded to nearest even.  Pad targets are 0.  Every tile has
-// L+1 time rows; row L is all zeros (the dummy neighbour row of odd-length
-// tables).
-template <bool BF16, int RW>
+// w][u] - mean; BF16 / FP16: word w holds targets 2w (low half) and 2w+1
+// (high half), each rounded to nearest even (FP16: after scaling by the
+// target's power of two).  Pad targets are 0.  Every tile has L+1 time rows;
+// row L is all zeros (the dummy neighbour row of odd-length tables).
+template <int FMT, int RW>
 __global__ void target_store_kernel(const float *__restrict__ Y, long long ld,
                                     const int32_t *__restrict__ rows, int N, int L,
-                                    const double *__restrict__ mean, uint8_t *__restrict__ Yt) {
-    constexpr int TT = BF16 ? 2 * RW : RW;  // targets per tile
+                                    const double *__restrict__ mean,
+                                    const double *__restrict__ scale, uint8_t *__restrict__ Yt) {
+    constexpr bool PK = FMT != EDM_FP32;
+    constexpr int TT = PK ? 2 * RW : RW;  // targets per tile
     __shared__ float s[TT][33];
     const int tile = blockIdx.x, u0 = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
     for (int j = ty; j < TT; j += 8) {
         const int tgt = tile * TT + j, u = u0 + tx;
         float v = 0.f;
-        if (tgt < N && u < L)
-            v = static_cast<float>(static_cast<double>(Y[target_row(rows, tgt) * ld + u]) -
-                                   mean[tgt]);
+        if (tgt < N && u < L) {
+            double c = static_cast<double>(Y[target_row(rows, tgt) * ld + u]) - mean[tgt];
+            if (FMT == EDM_FP16_TARGETS) c *= scale[tgt];
+            v = static_cast<float>(c);
+        }
         s[j][tx] = v;
     }
     __syncthreads();
@@ -92,9 +127,13 @@ __global__ void target_store_kernel(const float *__restrict__ Y, long long ld,
     for (int r = ty; r < 32; r += 8) {
         const int u = u0 + r;
         if (u >= L) continue;
-        if (BF16) {
+        if (FMT == EDM_BF16_TARGETS) {
             const unsigned lo = __bfloat16_as_ushort(__float2bfloat16_rn(s[2 * tx][r]));
             const unsigned hi = __bfloat16_as_ushort(__float2bfloat16_rn(s[2 * tx + 1][r]));
+            reinterpret_cast<uint32_t *>(base + static_cast<size_t>(u) * ROW)[tx] = lo | (hi << 16);
+        } else if (FMT == EDM_FP16_TARGETS) {
+            const unsigned lo = __half_as_ushort(__float2half_rn(s[2 * tx][r]));
+            const unsigned hi = __half_as_ushort(__float2half_rn(s[2 * tx + 1][r]));
             reinterpret_cast<uint32_t *>(base + static_cast<size_t>(u) * ROW)[tx] = lo | (hi << 16);
         } else {
             reinterpret_cast<float *>(base + static_cast<size_t>(u) * ROW)[tx] = s[tx][r];
@@ -103,21 +142,20 @@ __global__ void target_store_kernel(const float *__restrict__ Y, long long ld,
 }
 
 // The stored value of target tgt at time u, as the lookup reads it.
-template <bool BF16, int RW>
+template <int FMT, int RW>
 __device__ __forceinline__ float stored_target(const uint8_t *Yt, int L, int tgt, int u) {
-    constexpr int TT = BF16 ? 2 * RW : RW;
+    constexpr int TT = FMT != EDM_FP32 ? 2 * RW : RW;
     const uint32_t *row = reinterpret_cast<const uint32_t *>(
         Yt + (static_cast<size_t>(tgt / TT) * (L + 1) + u) * (4 * RW));
-    if (!BF16) return __uint_as_float(row[tgt % TT]);
-    const uint32_t v = row[(tgt % TT) >> 1];
-    return __uint_as_float((tgt & 1) ? (v & 0xffff0000u) : (v << 16));
+    if (FMT == EDM_FP32) return __uint_as_float(row[tgt % TT]);
+    return unpack_target<FMT>(row[(tgt % TT) >> 1], tgt & 1);
 }
 
 // One warp per target: FP64 sums of the stored values and their squares
 // over the observation window of every E, times (E-1)tau+Tp .. L-1.  The
 // windows are nested, so one pass over the longest suffix plus the pieces
 // between consecutive starts gives all of them.
-template <bool BF16, int RW>
+template <int FMT, int RW>
 __global__ void target_sums_kernel(const uint8_t *__restrict__ Yt, int N, int L, int tau, int Tp,
                                    double *__restrict__ ysum, double *__restrict__ yysum) {
     const int tgt = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = lane_id();
@@ -127,7 +165,7 @@ __global__ void target_sums_kernel(const uint8_t *__restrict__ Yt, int N, int L,
     const int start_top = (e_top - 1) * tau + Tp;
     double s1 = 0.0, s2 = 0.0;
     for (int u = start_top + lane; u < L; u += 32) {
-        const double v = stored_target<BF16, RW>(Yt, L, tgt, u);
+        const double v = stored_target<FMT, RW>(Yt, L, tgt, u);
         s1 += v;
         s2 += v * v;
     }
@@ -139,7 +177,7 @@ __global__ void target_sums_kernel(const uint8_t *__restrict__ Yt, int N, int L,
         if (E < e_top) {
             // add times start .. start(E+1)-1
             for (int u = start; u < E * tau + Tp && u < L; ++u) {
-                const double v = stored_target<BF16, RW>(Yt, L, tgt, u);
+                const double v = stored_target<FMT, RW>(Yt, L, tgt, u);
                 s1 += v;
                 s2 += v * v;
             }
@@ -153,9 +191,11 @@ __global__ void target_sums_kernel(const uint8_t *__restrict__ Yt, int N, int L,
 // Shared memory a lookup CTA needs besides its tile: the hand-over buffer,
 // at least two 4 KB table stages and the mbarriers.
 static size_t lookup_fixed_bytes(edm_precision prec) {
-    const size_t red = sizeof(float) * (prec == EDM_BF16_TARGETS ? LkCfg<true>::RED_FLOATS
-                                                                  : LkCfg<false>::RED_FLOATS);
-    return red + (2 * LK_MAX_STAGES + 4) * sizeof(uint64_t);
+    const size_t red = sizeof(float) * (prec != EDM_FP32 ? LkCfg<EDM_BF16_TARGETS>::RED_FLOATS
+                                                          : LkCfg<EDM_FP32>::RED_FLOATS);
+    // stage barriers (full, empty), the tile barrier, the three hand-over
+    // barriers and the abort word: 2 stages + 5 words (6 reserved)
+    return red + (2 * LK_MAX_STAGES + 6) * sizeof(uint64_t);
 }
 
 int lookup_row_words(edm_ctx *ctx, int L, edm_precision prec) {
@@ -167,7 +207,7 @@ int lookup_row_words(edm_ctx *ctx, int L, edm_precision prec) {
 }
 
 static int targets_per_tile(edm_precision prec, int rw) {
-    return prec == EDM_BF16_TARGETS ? 2 * rw : rw;
+    return prec != EDM_FP32 ? 2 * rw : rw;
 }
 
 size_t target_store_bytes(int N_tgt, int L, edm_precision prec, int rw) {
@@ -176,38 +216,49 @@ size_t target_store_bytes(int N_tgt, int L, edm_precision prec, int rw) {
     return align_up(tiles * (L + 1) * 4 * rw, 256);
 }
 
+// The kernels of the target store for one storage format and row width.
+template <int FMT, int RW>
+static edm_status launch_store_fmt(edm_ctx *ctx, const float *Y, long long ld, const int32_t *rows,
+                                   int N_tgt, int L, int tau, int Tp, uint8_t *Yt,
+                                   const double *mean, const double *scale, double *ysum,
+                                   double *yysum) {
+    const int tt = FMT != EDM_FP32 ? 2 * RW : RW;
+    dim3 grid((N_tgt + tt - 1) / tt, (L + 31) / 32), block(32, 8);
+    before_launch(ctx);
+    target_store_kernel<FMT, RW><<<grid, block, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean,
+                                                                  scale, Yt);
+    edm_status st = after_launch(ctx, "target_store_kernel");
+    if (st != EDM_OK) return st;
+    const int warps_blocks = (N_tgt * 32 + 255) / 256;
+    before_launch(ctx);
+    target_sums_kernel<FMT, RW><<<warps_blocks, 256, 0, ctx->stream>>>(Yt, N_tgt, L, tau, Tp,
+                                                                      ysum, yysum);
+    return after_launch(ctx, "target_sums_kernel");
+}
+
 edm_status launch_target_store(edm_ctx *ctx, const float *Y, long long ld, const int32_t *rows,
                                int N_tgt, int L, int tau, int Tp, edm_precision prec, int rw,
                                uint8_t *Yt, double *mean_ws, double *ysum, double *yysum) {
+    // mean_ws holds the means [N_tgt] followed by the FP16 scales [N_tgt]
+    double *scale = mean_ws + N_tgt;
     const int warps_blocks = (N_tgt * 32 + 255) / 256;
     before_launch(ctx);
-    target_mean_kernel<<<warps_blocks, 256, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean_ws);
+    target_mean_kernel<<<warps_blocks, 256, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean_ws,
+                                                              scale);
     edm_status st = after_launch(ctx, "target_mean_kernel");
     if (st != EDM_OK) return st;
-    const int tt = targets_per_tile(prec, rw);
-    dim3 grid((N_tgt + tt - 1) / tt, (L + 31) / 32), block(32, 8);
-    const bool bf16 = prec == EDM_BF16_TARGETS;
-    before_launch(ctx);
-    if (bf16 && rw == 16)
-        target_store_kernel<true, 16><<<grid, block, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean_ws, Yt);
-    else if (bf16)
-        target_store_kernel<true, 32><<<grid, block, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean_ws, Yt);
-    else if (rw == 16)
-        target_store_kernel<false, 16><<<grid, block, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean_ws, Yt);
-    else
-        target_store_kernel<false, 32><<<grid, block, 0, ctx->stream>>>(Y, ld, rows, N_tgt, L, mean_ws, Yt);
-    st = after_launch(ctx, "target_store_kernel");
-    if (st != EDM_OK) return st;
-    before_launch(ctx);
-    if (bf16 && rw == 16)
-        target_sums_kernel<true, 16><<<warps_blocks, 256, 0, ctx->stream>>>(Yt, N_tgt, L, tau, Tp, ysum, yysum);
-    else if (bf16)
-        target_sums_kernel<true, 32><<<warps_blocks, 256, 0, ctx->stream>>>(Yt, N_tgt, L, tau, Tp, ysum, yysum);
-    else if (rw == 16)
-        target_sums_kernel<false, 16><<<warps_blocks, 256, 0, ctx->stream>>>(Yt, N_tgt, L, tau, Tp, ysum, yysum);
-    else
-        target_sums_kernel<false, 32><<<warps_blocks, 256, 0, ctx->stream>>>(Yt, N_tgt, L, tau, Tp, ysum, yysum);
-    return after_launch(ctx, "target_sums_kernel");
+    const bool half = rw == 16;
+    switch (prec) {
+    case EDM_BF16_TARGETS:
+        return half ? launch_store_fmt<EDM_BF16_TARGETS, 16>(ctx, Y, ld, rows, N_tgt, L, tau, Tp, Yt, mean_ws, scale, ysum, yysum)
+                    : launch_store_fmt<EDM_BF16_TARGETS, 32>(ctx, Y, ld, rows, N_tgt, L, tau, Tp, Yt, mean_ws, scale, ysum, yysum);
+    case EDM_FP16_TARGETS:
+        return half ? launch_store_fmt<EDM_FP16_TARGETS, 16>(ctx, Y, ld, rows, N_tgt, L, tau, Tp, Yt, mean_ws, scale, ysum, yysum)
+                    : launch_store_fmt<EDM_FP16_TARGETS, 32>(ctx, Y, ld, rows, N_tgt, L, tau, Tp, Yt, mean_ws, scale, ysum, yysum);
+    default:
+        return half ? launch_store_fmt<EDM_FP32, 16>(ctx, Y, ld, rows, N_tgt, L, tau, Tp, Yt, mean_ws, scale, ysum, yysum)
+                    : launch_store_fmt<EDM_FP32, 32>(ctx, Y, ld, rows, N_tgt, L, tau, Tp, Yt, mean_ws, scale, ysum, yysum);
+    }
 }
 
 // ------------------------------------------------------- lookup + Pearson
@@ -235,9 +286,9 @@ __device__ __forceinline__ long long rho_column(const LookupArgs &a, int tgt) {
 // targets, the sums of the prediction, of its square and of its product with
 // the observation, kept as (row 2p, row 2p+1) pairs for the packed FP32x2
 // arithmetic.
-template <bool BF16>
+template <bool PK>
 struct PairMoments {
-    static constexpr int T = BF16 ? 2 : 1;  // targets per lane
+    static constexpr int T = PK ? 2 : 1;  // targets per lane
     float2 s[T], ss[T], sy[T];
 };
 
@@ -250,9 +301,10 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 // the two rows run side by side in FFMA2/FADD2 lanes.  y_q - y_last is formed
 // as fma(y_last, -1, y_q): the exact difference rounded once, as a
 // subtraction.
-template <int K, bool BF16, bool SMEM_TILE>
+template <int K, int FMT, bool SMEM_TILE>
 __device__ __forceinline__ void lookup_pair(const uint8_t *blk, const uint32_t *tl, uint32_t yA,
-                                            uint32_t yB, PairMoments<BF16> &m) {
+                                            uint32_t yB, PairMoments<FMT != EDM_FP32> &m) {
+    constexpr bool PK = FMT != EDM_FP32;
     constexpr int PB = table_pair_bytes(K);
     constexpr int NV = PB / 16;
     uint32_t wd[4 * NV];
@@ -275,11 +327,9 @@ __device__ __forceinline__ void lookup_pair(const uint8_t *blk, const uint32_t *
     }
     const float2 m1 = f2(-1.f, -1.f);
 #pragma unroll
-    for (int c = 0; c < PairMoments<BF16>::T; ++c) {
-        // c selects the lane's target: FP32 word, or BF16 low / high half
-        auto val = [&](uint32_t v) {
-            return __uint_as_float(BF16 ? (c == 0 ? (v << 16) : (v & 0xffff0000u)) : v);
-        };
+    for (int c = 0; c < PairMoments<PK>::T; ++c) {
+        // c selects the lane's target: FP32 word, or 16-bit low / high half
+        auto val = [&](uint32_t v) { return unpack_target<FMT>(v, c); };
         const float2 yl = f2(val(gA[K - 1]), val(gB[K - 1]));
         float2 acc = yl;
 #pragma unroll
@@ -299,9 +349,10 @@ __device__ __forceinline__ void lookup_pair(const uint8_t *blk, const uint32_t *
 // of the pair block and lane l its tile word l%16, so one gather reads two
 // rows of 16 words.  Same prediction formula as lookup_pair; the moments
 // go to the .x lanes of the pair accumulators.
-template <int K, bool BF16>
+template <int K, int FMT>
 __device__ __forceinline__ void lookup_pair_half(const uint8_t *blk, const uint32_t *tl, int h,
-                                                 uint32_t yv, PairMoments<BF16> &m) {
+                                                 uint32_t yv, PairMoments<FMT != EDM_FP32> &m) {
+    constexpr bool PK = FMT != EDM_FP32;
     constexpr int PB = table_pair_bytes(K);
     constexpr int NV = PB / 16;
     uint32_t wd[4 * NV];
@@ -322,10 +373,8 @@ __device__ __forceinline__ void lookup_pair_half(const uint8_t *blk, const uint3
         g[q] = tl[u * 16];
     }
 #pragma unroll
-    for (int c = 0; c < PairMoments<BF16>::T; ++c) {
-        auto val = [&](uint32_t v) {
-            return __uint_as_float(BF16 ? (c == 0 ? (v << 16) : (v & 0xffff0000u)) : v);
-        };
+    for (int c = 0; c < PairMoments<PK>::T; ++c) {
+        auto val = [&](uint32_t v) { return unpack_target<FMT>(v, c); };
         const float yl = val(g[K - 1]);
         float acc = yl;
 #pragma unroll
@@ -357,12 +406,13 @@ struct RingPos {
 // take pairs warp, warp + NC, ... of each stage; a pair's observations are
 // read once and serve every member of the group.  All G slots are processed
 // (the empty slots of a partial group hold a copy of its first member).
-template <int K, bool BF16, bool SMEM_TILE, bool HALF>
+template <int K, int FMT, bool SMEM_TILE, bool HALF>
 __device__ __forceinline__ void consume_group(const LookupArgs &a, const uint8_t *tile,
                                               const uint8_t *stages, uint64_t *full,
                                               uint64_t *empty, RingPos &rp, int n, int t0,
-                                              PairMoments<BF16> (&pm)[LkCfg<BF16>::G]) {
-    using C = LkCfg<BF16>;
+                                              volatile int *a_abort,
+                                              PairMoments<LkCfg<FMT>::PK> (&pm)[LkCfg<FMT>::G]) {
+    using C = LkCfg<FMT>;
     constexpr int PB = table_pair_bytes(K);
     constexpr int GPB = C::G * PB;
     const int CP = a.stage_bytes / GPB;
@@ -373,16 +423,16 @@ __device__ __forceinline__ void consume_group(const LookupArgs &a, const uint8_t
     if (HALF) {
         for (int p0 = 0; p0 < npairs; p0 += CP) {
             const int s = rp.s;
-            mbar_wait_bounded(&full[s], rp.ph, a.flags);
+            const bool ok = mbar_wait_bounded(&full[s], rp.ph, a.flags, a_abort);
             const uint8_t *st = stages + static_cast<size_t>(s) * a.stage_bytes;
-            const int pairs = min(CP, npairs - p0);
+            const int pairs = ok ? min(CP, npairs - p0) : 0;  // no data: skip the stage
             const int ybase = t0 + a.Tp + 2 * p0 + h;
             for (int p = warp; p < pairs; p += C::NC) {
                 const uint32_t yv = tl[(ybase + 2 * p) * 16];
                 const uint8_t *blk = st + static_cast<size_t>(p) * GPB;
 #pragma unroll
                 for (int m = 0; m < C::G; ++m)
-                    lookup_pair_half<K, BF16>(blk + m * PB, tl, h, yv, pm[m]);
+                    lookup_pair_half<K, FMT>(blk + m * PB, tl, h, yv, pm[m]);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
@@ -392,9 +442,9 @@ __device__ __forceinline__ void consume_group(const LookupArgs &a, const uint8_t
     }
     for (int p0 = 0; p0 < npairs; p0 += CP) {
         const int s = rp.s;
-        mbar_wait_bounded(&full[s], rp.ph, a.flags);
+        const bool ok = mbar_wait_bounded(&full[s], rp.ph, a.flags, a_abort);
         const uint8_t *st = stages + static_cast<size_t>(s) * a.stage_bytes;
-        const int pairs = min(CP, npairs - p0);
+        const int pairs = ok ? min(CP, npairs - p0) : 0;  // no data: skip the stage
         const int ybase = t0 + a.Tp + 2 * p0;
         for (int p = warp; p < pairs; p += C::NC) {
             const int yrow = ybase + 2 * p;
@@ -403,12 +453,23 @@ __device__ __forceinline__ void consume_group(const LookupArgs &a, const uint8_t
             const uint8_t *blk = st + static_cast<size_t>(p) * GPB;
 #pragma unroll
             for (int m = 0; m < C::G; ++m)
-                lookup_pair<K, BF16, SMEM_TILE>(blk + m * PB, tl, yA, yB, pm[m]);
+                lookup_pair<K, FMT, SMEM_TILE>(blk + m * PB, tl, yA, yB, pm[m]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
         rp.next(a.stages);
     }
+}
+
+// hi + lo += v, with hi + lo kept as an unevaluated sum of two floats: the
+// rounding error of hi + v is recovered exactly (Knuth's TwoSum, six FP32
+// operations, every one rounded to nearest) and added into lo.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float v) {
+    const float s = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    hi = s;
+    lo = __fadd_rn(lo, err);
 }
 
 // rho from the prediction moments (FP32 partials of the consumer warps) and
@@ -420,12 +481,13 @@ __device__ __forceinline__ float finish_rho(double n, double sa, double saa, dou
 
 // HALF: 16-word tile rows (see lookup_pair_half); only with the tile in
 // shared memory.
-template <bool BF16, bool SMEM_TILE, bool HALF>
-__global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const LookupArgs a) {
+template <int FMT, bool SMEM_TILE, bool HALF>
+__global__ void __launch_bounds__(LkCfg<FMT>::THREADS, 1) lookup_kernel(const LookupArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
-    using C = LkCfg<BF16>;
+    using C = LkCfg<FMT>;
+    constexpr bool PK = C::PK;
     constexpr int RW = HALF ? 16 : 32;            // words per tile row
-    constexpr int TT = BF16 ? 2 * RW : RW;        // targets per tile
+    constexpr int TT = PK ? 2 * RW : RW;          // targets per tile
     constexpr int G = C::G, NM = C::NM;
     const int g0 = blockIdx.y * a.GB;
     const int g1 = min(*a.grp.count, g0 + a.GB);
@@ -438,7 +500,11 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
     float *red = reinterpret_cast<float *>(stages + static_cast<size_t>(a.stages) * a.stage_bytes);
     uint64_t *bars = reinterpret_cast<uint64_t *>(red + C::RED_FLOATS);
     uint64_t *full = bars, *empty = bars + a.stages, *tbar = bars + 2 * a.stages;
-    uint64_t *red_full = tbar + 1, *red_empty = tbar + 2, *half_full = tbar + 3;
+    // hand-over barriers, one phase per group each: half_full (warps 8..15
+    // wrote their slots), red_full (warps 0..7 added theirs), red_empty (the
+    // finisher read them)
+    uint64_t *half_full = tbar + 1, *red_full = tbar + 2, *red_empty = tbar + 3;
+    volatile int *abort_w = reinterpret_cast<volatile int *>(tbar + 4);
     const int warp = threadIdx.x >> 5, lane = lane_id();
 
     if (threadIdx.x == 0) {
@@ -447,9 +513,10 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
             mbar_init(&empty[s], C::NC);
         }
         mbar_init(tbar, 1);
+        mbar_init(half_full, C::NC - C::HALF);
         mbar_init(red_full, C::HALF);
         mbar_init(red_empty, 1);
-        mbar_init(half_full, C::NC - C::HALF);
+        *abort_w = 0;
         fence_barrier_init();
     }
     __syncthreads();
@@ -466,7 +533,8 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
             }
             RingPos rp;
             bool first_pass = true;  // the stages are empty until the ring wraps
-            for (int gi = g0; gi < g1; ++gi) {
+            bool stop = false;       // a wait gave up: issue no more copies
+            for (int gi = g0; gi < g1 && !stop; ++gi) {
                 const int E = a.grp.E[gi];
                 if (E == 0) continue;
                 const int n = a.L - (E - 1) * a.tau - a.Tp;
@@ -476,7 +544,10 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
                 const uint8_t *src = a.tables + a.grp.off[gi];
                 for (int p0 = 0; p0 < npairs; p0 += CP) {
                     const int s = rp.s;
-                    if (!first_pass) mbar_wait_bounded(&empty[s], rp.ph ^ 1u, a.flags);
+                    if (!first_pass && !mbar_wait_bounded(&empty[s], rp.ph ^ 1u, a.flags, abort_w)) {
+                        stop = true;
+                        break;
+                    }
                     const uint32_t bytes = static_cast<uint32_t>(min(CP, npairs - p0) * GPB);
                     mbar_arrive_expect_tx(&full[s], bytes);
                     bulk_copy_g2s(stages + static_cast<size_t>(s) * a.stage_bytes,
@@ -485,12 +556,24 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
                     if (rp.s == 0) first_pass = false;
                 }
             }
+            // the CTA's shared memory must outlive every copy issued into it:
+            // wait (bounded, past any abort) for the last fill of each stage
+            // and for the tile
+            for (int s = 0; s < a.stages; ++s) {
+                if (s < rp.s)
+                    mbar_wait_bounded(&full[s], rp.ph, a.flags, nullptr);
+                else if (!first_pass)
+                    mbar_wait_bounded(&full[s], rp.ph ^ 1u, a.flags, nullptr);
+            }
+            if (SMEM_TILE) mbar_wait_bounded(tbar, 0, a.flags, nullptr);
         }
         return;
     }
 
     if (warp == C::FINISHER) {
-        // ---------------- finisher: rho of every member of every group
+        // ---------------- finisher: rho of every member of every group from
+        // the HALF slots of FP32 partial moments (consumer warps w and w+8
+        // added together), summed in slot order
         int done = 0;
         for (int gi = g0; gi < g1; ++gi) {
             const int E = a.grp.E[gi], nm = a.grp.n[gi];
@@ -506,41 +589,59 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
                 if (lane == 0 && blockIdx.x == 0) set_flag(a.flags, EDMF_BADARG);
                 continue;
             }
-            mbar_wait_bounded(red_full, done & 1, a.flags);
-            float S[G][NM];
+            // the eight partials are summed exactly enough for FP64: each sum
+            // is kept as an unevaluated pair hi + lo of floats (Knuth's
+            // TwoSum: hi + lo equals the running sum to about 2^-48), which
+            // the FP32 pipe does at full rate; FP64 runs at a small fraction
+            // of that on this GPU and held the next group's hand-over up
+            float Shi[G][NM], Slo[G][NM];
 #pragma unroll
             for (int m = 0; m < G; ++m)
 #pragma unroll
-                for (int j = 0; j < NM; ++j) S[m][j] = 0.f;
+                for (int j = 0; j < NM; ++j) Shi[m][j] = Slo[m][j] = 0.f;
+            const bool ok = mbar_wait_bounded(red_full, done & 1, a.flags, abort_w);
             for (int w = 0; w < C::HALF; ++w)
 #pragma unroll
                 for (int m = 0; m < G; ++m)
                     if (m < nm)
 #pragma unroll
-                        for (int j = 0; j < NM; ++j) S[m][j] += red[((w * G + m) * NM + j) * 32 + lane];
+                        for (int j = 0; j < NM; ++j)
+                            two_sum_acc(Shi[m][j], Slo[m][j], red[((w * G + m) * NM + j) * 32 + lane]);
             __syncwarp();
             if (lane == 0) mbar_arrive(red_empty);
+            double S[G][NM];
+#pragma unroll
+            for (int m = 0; m < G; ++m)
+#pragma unroll
+                for (int j = 0; j < NM; ++j)
+                    S[m][j] = static_cast<double>(Shi[m][j]) + static_cast<double>(Slo[m][j]);
             const double dn = static_cast<double>(a.L - (E - 1) * a.tau - a.Tp);
             const size_t wo = static_cast<size_t>(E - 1) * a.N_tgt;
+            const float nan = __int_as_float(0x7fc00000);
 #pragma unroll
             for (int m = 0; m < G; ++m) {
                 if (m >= nm) continue;
                 float *rho_row = a.rho + static_cast<long long>(libs[m] - a.lib0) * a.rho_ld;
                 if (HALF && lane >= 16) continue;
-                if (!BF16) {
+                if (!PK) {
                     const int tgt = tile_id * TT + lane;
                     if (tgt < a.N_tgt)
-                        rho_row[rho_column(a, tgt)] = finish_rho(dn, S[m][0], S[m][1], S[m][2],
-                                                                 a.ysum[wo + tgt], a.yysum[wo + tgt]);
+                        rho_row[rho_column(a, tgt)] =
+                            ok ? finish_rho(dn, S[m][0], S[m][1], S[m][2], a.ysum[wo + tgt],
+                                            a.yysum[wo + tgt])
+                               : nan;
                 } else {
                     const int tgt = tile_id * TT + 2 * lane;
                     if (tgt < a.N_tgt)
-                        rho_row[rho_column(a, tgt)] = finish_rho(dn, S[m][0], S[m][1], S[m][2],
-                                                                 a.ysum[wo + tgt], a.yysum[wo + tgt]);
+                        rho_row[rho_column(a, tgt)] =
+                            ok ? finish_rho(dn, S[m][0], S[m][1], S[m][2], a.ysum[wo + tgt],
+                                            a.yysum[wo + tgt])
+                               : nan;
                     if (tgt + 1 < a.N_tgt)
                         rho_row[rho_column(a, tgt + 1)] =
-                            finish_rho(dn, S[m][3], S[m][4], S[m][5], a.ysum[wo + tgt + 1],
-                                       a.yysum[wo + tgt + 1]);
+                            ok ? finish_rho(dn, S[m][3], S[m][4], S[m][5], a.ysum[wo + tgt + 1],
+                                            a.yysum[wo + tgt + 1])
+                               : nan;
                 }
             }
             ++done;
@@ -550,10 +651,10 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
 
     // -------------------- consumers
     const uint8_t *tile = SMEM_TILE ? tile_s : tile_g;
-    if (SMEM_TILE) mbar_wait_bounded(tbar, 0, a.flags);
+    if (SMEM_TILE) mbar_wait_bounded(tbar, 0, a.flags, abort_w);
     RingPos rp;
     int done = 0;
-    PairMoments<BF16> pm[G];
+    PairMoments<PK> pm[G];
     for (int gi = g0; gi < g1; ++gi) {
         const int E = a.grp.E[gi];
         if (E == 0) continue;
@@ -562,11 +663,11 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
 #pragma unroll
         for (int m = 0; m < G; ++m)
 #pragma unroll
-            for (int c = 0; c < PairMoments<BF16>::T; ++c)
+            for (int c = 0; c < PairMoments<PK>::T; ++c)
                 pm[m].s[c] = pm[m].ss[c] = pm[m].sy[c] = f2(0.f, 0.f);
         switch (E + 1) {
 #define EDM_CASE(k) \
-    case k: consume_group<k, BF16, SMEM_TILE, HALF>(a, tile, stages, full, empty, rp, n, t0, pm); break;
+    case k: consume_group<k, FMT, SMEM_TILE, HALF>(a, tile, stages, full, empty, rp, n, t0, abort_w, pm); break;
             EDM_CASE(2) EDM_CASE(3) EDM_CASE(4) EDM_CASE(5) EDM_CASE(6) EDM_CASE(7) EDM_CASE(8)
             EDM_CASE(9) EDM_CASE(10) EDM_CASE(11) EDM_CASE(12) EDM_CASE(13) EDM_CASE(14)
             EDM_CASE(15) EDM_CASE(16) EDM_CASE(17) EDM_CASE(18) EDM_CASE(19) EDM_CASE(20)
@@ -574,23 +675,26 @@ __global__ void __launch_bounds__(LkCfg<BF16>::THREADS, 1) lookup_kernel(const L
 #undef EDM_CASE
         default: break;
         }
-        // hand the partial moments on (one buffer of HALF slots): warp w+HALF
-        // writes slot w once the finisher has read the previous group; warp w
-        // adds slot w to its own partials, writes the sum back and signals
-        // the finisher
+        // hand the partial moments over; group d = done is phase d of every
+        // hand-over barrier.  Warp w+8 writes slot w once the finisher has
+        // read the previous group (red_empty phase d-1); warp w waits for it
+        // (half_full phase d), adds its own partials to the slot in FP32 and
+        // signals the finisher (red_full).  No barrier can be more than one
+        // phase past the one waited for (its next phase needs this warp's own
+        // arrival first), so each parity test is unambiguous.
         const bool upper = warp >= C::HALF;
         float *rb0 = red + (upper ? warp - C::HALF : warp) * G * NM * 32;
         if (upper) {
-            if (done > 0) mbar_wait_bounded(red_empty, (done - 1) & 1, a.flags);
+            if (done > 0) mbar_wait_bounded(red_empty, (done - 1) & 1, a.flags, abort_w);
         } else {
-            mbar_wait_bounded(half_full, done & 1, a.flags);
+            mbar_wait_bounded(half_full, done & 1, a.flags, abort_w);
         }
 #pragma unroll
         for (int m = 0; m < G; ++m) {
             if (m >= nm) continue;
             float *rb = rb0 + m * NM * 32;
 #pragma unroll
-            for (int c = 0; c < PairMoments<BF16>::T; ++c) {
+            for (int c = 0; c < PairMoments<PK>::T; ++c) {
                 // row pairs: the two rows of a lane (FFMA2 lanes), or the
                 // two half-warps (HALF)
                 float v0, v1, v2;
@@ -644,17 +748,17 @@ edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, cons
                          const CcmGroups &g, int lib0, int nlib, int tau, int Tp,
                          edm_precision prec, int rw, const double *ysum, const double *yysum,
                          float *rho, long long rho_ld, const int32_t *rho_col) {
-    const bool bf16 = prec == EDM_BF16_TARGETS;
+    const bool pk = prec != EDM_FP32;  // two 16-bit targets per word
     const bool half = rw == 16;
     const int tt = targets_per_tile(prec, rw);
     const int n_tiles = (N_tgt + tt - 1) / tt;
-    const int threads = bf16 ? LkCfg<true>::THREADS : LkCfg<false>::THREADS;
-    const int G = bf16 ? LkCfg<true>::G : LkCfg<false>::G;
+    const int threads = pk ? LkCfg<EDM_BF16_TARGETS>::THREADS : LkCfg<EDM_FP32>::THREADS;
+    const int G = pk ? LkCfg<EDM_BF16_TARGETS>::G : LkCfg<EDM_FP32>::G;
     if (g.G != G) return set_error(ctx, EDM_ERR_INTERNAL, "lookup: group size mismatch");
     const size_t red_bytes =
-        sizeof(float) * (bf16 ? LkCfg<true>::RED_FLOATS : LkCfg<false>::RED_FLOATS);
+        sizeof(float) * (pk ? LkCfg<EDM_BF16_TARGETS>::RED_FLOATS : LkCfg<EDM_FP32>::RED_FLOATS);
     const size_t tile_bytes = static_cast<size_t>(L + 1) * 4 * rw;
-    const size_t fixed = red_bytes + (2 * LK_MAX_STAGES + 4) * sizeof(uint64_t);
+    const size_t fixed = red_bytes + (2 * LK_MAX_STAGES + 6) * sizeof(uint64_t);
     const size_t limit = static_cast<size_t>(ctx->max_smem_optin);
     // stages of 6 KB (4 KB when the tile leaves less room); at least two
     const size_t min_stage = 4096, big_stage = 6144;
@@ -665,7 +769,7 @@ edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, cons
     const int stages = static_cast<int>(std::min<size_t>(LK_MAX_STAGES, avail / stage_bytes));
     if (stages < 2) return set_error(ctx, EDM_ERR_INTERNAL, "lookup: no room for table stages");
     const size_t smem = (smem_tile ? tile_bytes : 0) + static_cast<size_t>(stages) * stage_bytes +
-                        red_bytes + (2 * stages + 4) * sizeof(uint64_t);
+                        red_bytes + (2 * stages + 6) * sizeof(uint64_t);
 
     // libraries per CTA: a fixed override, else the autotuned value of this
     // launch's bucket, else the heuristic; a CTA takes lb / G groups
@@ -697,12 +801,23 @@ edm_status launch_lookup(edm_ctx *ctx, const uint8_t *Yt, int N_tgt, int L, cons
     a.flags = ctx->d_flags;
     dim3 grid(n_tiles, static_cast<unsigned>((g.ngroups_max + GB - 1) / GB));
     void (*kern)(const LookupArgs);
-    if (half)
-        kern = bf16 ? lookup_kernel<true, true, true> : lookup_kernel<false, true, true>;
-    else if (bf16)
-        kern = smem_tile ? lookup_kernel<true, true, false> : lookup_kernel<true, false, false>;
-    else
-        kern = smem_tile ? lookup_kernel<false, true, false> : lookup_kernel<false, false, false>;
+    switch (prec) {
+    case EDM_BF16_TARGETS:
+        kern = half ? lookup_kernel<EDM_BF16_TARGETS, true, true>
+                    : (smem_tile ? lookup_kernel<EDM_BF16_TARGETS, true, false>
+                                 : lookup_kernel<EDM_BF16_TARGETS, false, false>);
+        break;
+    case EDM_FP16_TARGETS:
+        kern = half ? lookup_kernel<EDM_FP16_TARGETS, true, true>
+                    : (smem_tile ? lookup_kernel<EDM_FP16_TARGETS, true, false>
+                                 : lookup_kernel<EDM_FP16_TARGETS, false, false>);
+        break;
+    default:
+        kern = half ? lookup_kernel<EDM_FP32, true, true>
+                    : (smem_tile ? lookup_kernel<EDM_FP32, true, false>
+                                 : lookup_kernel<EDM_FP32, false, false>);
+        break;
+    }
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     before_launch(ctx);
     kern<<<grid, threads, smem, ctx->stream>>>(a);

@@ -74,12 +74,17 @@ edm_status launch_smem_probe(edm_ctx *ctx, double ms, double *bytes_per_s) {
 
 // One thread waits, with the bounded wait every pipelined kernel of the
 // library uses, on an mbarrier that expects one arrival which never comes.
-// The wait gives up after `ms` milliseconds and raises the timeout flag.
+// The wait gives up after `ms` milliseconds, raises the timeout flag and sets
+// the CTA's abort word; a second wait on the same barrier then returns at
+// once, so the kernel ends after about one limit, not two.
 __global__ void wait_check_kernel(uint64_t limit_ns, int *flags) {
     __shared__ uint64_t bar;
+    __shared__ int abort_word;
+    abort_word = 0;
     mbar_init(&bar, 1);
     fence_barrier_init();
-    mbar_wait_bounded(&bar, 0, flags, limit_ns);
+    mbar_wait_bounded(&bar, 0, flags, &abort_word, limit_ns);
+    mbar_wait_bounded(&bar, 0, flags, &abort_word, limit_ns);
 }
 
 edm_status launch_wait_check(edm_ctx *ctx, int ms) {

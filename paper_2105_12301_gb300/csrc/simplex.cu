@@ -6,11 +6,12 @@
 // Y = X and horizon Tp_sel), E = 1..E_max, E* = argmax rho_E.
 //
 // One CTA owns one series (staged in shared memory) and a block of query
-// times; one warp per query time runs knn_row in KNN_SET mode (exact FP64
-// neighbour sets, FP32 distances unless the band had to be resolved), then
-// the weighted prediction.  Prediction and observation are centred on the
-// series mean before their moments are accumulated (FP32 per warp, FP64
-// across warps and CTAs); rho is finished in FP64 by a second kernel.
+// times; one warp per query time keeps the FP32 squared distances to every
+// candidate, adds one lag per E, and selects the exact FP64 neighbour set of
+// every E from them, then forms the weighted prediction.  Prediction and
+// observation are centred on the series mean before their moments are
+// accumulated (FP32 per warp, FP64 across warps and CTAs); rho is finished in
+// FP64 by a second kernel.
 #include <mutex>
 
 #include "knn_core.cuh"
@@ -44,86 +45,6 @@ __device__ __forceinline__ float simplex_predict(float d, int u, const float *xs
     return wy / w;
 }
 
-template <int E>
-__device__ __forceinline__ void simplex_row(const float *xs, int t, int lo, int hi, int tau, int Tp,
-                                            float mu, WarpScratch *ws, float (&m)[5]) {
-    constexpr int K = E + 1;
-    const int lane = lane_id();
-    int u = 0;
-    float d = 0.f;
-    knn_row<E, KNN_SET>(xs, t, lo, hi, tau, K, ws, &u, &d);
-    const float a = simplex_predict(d, u, xs, Tp, mu, K);
-    const float b = __fsub_rn(xs[t + Tp], mu);
-    if (lane == E - 1) {
-        m[0] += a;
-        m[1] += b;
-        m[2] = __fmaf_rn(a, a, m[2]);
-        m[3] = __fmaf_rn(b, b, m[3]);
-        m[4] = __fmaf_rn(a, b, m[4]);
-    }
-}
-
-// partial [N][nrb][E_max][5] FP64 moments of (prediction, observation).
-template <bool SMEM>
-__global__ void __launch_bounds__(SX_WARPS * 32)
-    simplex_kernel(const float *__restrict__ X, int L, int E_max, int tau, int Tp, int TB, int nrb,
-                   double *__restrict__ partial) {
-    extern __shared__ __align__(16) uint8_t smem[];
-    WarpScratch *wsa = reinterpret_cast<WarpScratch *>(smem);
-    float *red = reinterpret_cast<float *>(smem + SX_WARPS * sizeof(WarpScratch));  // [W][32][5]
-    double *mu_s = reinterpret_cast<double *>(red + SX_WARPS * 32 * 5);               // [W]
-    float *xs_s = reinterpret_cast<float *>(mu_s + SX_WARPS);
-    const int series = blockIdx.x, rb = blockIdx.y;
-    const int warp = threadIdx.x >> 5, lane = lane_id();
-    const float *xg = X + static_cast<size_t>(series) * L;
-
-    // series mean in FP64, fixed reduction order (same in every CTA)
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < L; i += blockDim.x) acc += static_cast<double>(xg[i]);
-    acc = warp_sum_d(acc);
-    if (lane == 0) mu_s[warp] = acc;
-    const float *xs = xg;
-    if (SMEM) {
-        for (int i = threadIdx.x; i < L; i += blockDim.x) xs_s[i] = xg[i];
-        xs = xs_s;
-    }
-    __syncthreads();
-    double tot = 0.0;
-    for (int w = 0; w < SX_WARPS; ++w) tot += mu_s[w];
-    const float mu = static_cast<float>(tot / L);
-
-    float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // lane e: moments of E = e+1
-    WarpScratch *ws = wsa + warp;
-    const int t_begin = rb * TB, t_end = t_begin + TB;  // this CTA's query times
-    for (int E = 1; E <= E_max; ++E) {
-        const int lo = (E - 1) * tau, hi = L - 1 - Tp;
-        if (hi - lo + 1 < E + 2) break;  // too few points for this and larger E
-        const int a0 = max(lo, t_begin), a1 = min(hi + 1, t_end);
-        for (int t = a0 + warp; t < a1; t += SX_WARPS) {
-            switch (E) {
-#define EDM_CASE(e) \
-    case e: simplex_row<e>(xs, t, lo, hi, tau, Tp, mu, ws, m); break;
-                EDM_CASE(1) EDM_CASE(2) EDM_CASE(3) EDM_CASE(4) EDM_CASE(5) EDM_CASE(6)
-                EDM_CASE(7) EDM_CASE(8) EDM_CASE(9) EDM_CASE(10) EDM_CASE(11) EDM_CASE(12)
-                EDM_CASE(13) EDM_CASE(14) EDM_CASE(15) EDM_CASE(16) EDM_CASE(17) EDM_CASE(18)
-                EDM_CASE(19) EDM_CASE(20)
-#undef EDM_CASE
-            default: break;
-            }
-        }
-    }
-    // cross-warp reduction in FP64, fixed order
-#pragma unroll
-    for (int j = 0; j < 5; ++j) red[(warp * 32 + lane) * 5 + j] = m[j];
-    __syncthreads();
-    for (int i = threadIdx.x; i < E_max * 5; i += blockDim.x) {
-        const int e = i / 5, j = i % 5;
-        double s = 0.0;
-        for (int w = 0; w < SX_WARPS; ++w) s += static_cast<double>(red[(w * 32 + e) * 5 + j]);
-        partial[((static_cast<size_t>(series) * nrb + rb) * E_max + e) * 5 + j] = s;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Incremental sweep over E (series of up to 32*CH points).  The selection from
 // registers (select_set_regs) is shared with the neighbour-table builder.
@@ -141,7 +62,8 @@ __global__ void __launch_bounds__(SX_WARPS * 32)
 
 template <int CH, bool HEAD1>
 __device__ __forceinline__ void sweep_row(const float *xs, int t, int hi, int E_max, int tau,
-                                          int Tp, float mu, WarpScratch *ws, float (&m)[5]) {
+                                          int Tp, float mu, WarpScratch *ws, float (&m)[5],
+                                          unsigned keep, FallbackCount &fc) {
     const int lane = lane_id();
     float s[CH];
 #pragma unroll
@@ -170,7 +92,7 @@ __device__ __forceinline__ void sweep_row(const float *xs, int t, int hi, int E_
         }
         int u_out = 0;
         float d_out = 0.f;
-        select_set_regs<CH>(s, xs, t, lo, hi, E, tau, K, ws, u_out, d_out);
+        fc.add(select_set_regs<CH>(s, xs, t, lo, hi, E, tau, K, ws, u_out, d_out, keep));
         const float a = simplex_predict(d_out, u_out, xs, Tp, mu, K);
         const float b = __fsub_rn(xs[t + Tp], mu);
         if (lane == E - 1) {
@@ -188,7 +110,7 @@ __device__ __forceinline__ void sweep_row(const float *xs, int t, int hi, int E_
 template <int CH, bool HEAD1>
 __global__ void __launch_bounds__(SX_WARPS * 32)
     sweep_kernel(const float *__restrict__ X, int L, int E_max, int tau, int Tp, int TB, int nrb,
-                 double *__restrict__ partial) {
+                 double *__restrict__ partial, unsigned long long *stats) {
     extern __shared__ __align__(16) uint8_t smem[];
     WarpScratch *wsa = reinterpret_cast<WarpScratch *>(smem);
     float *red = reinterpret_cast<float *>(smem + SX_WARPS * sizeof(WarpScratch));
@@ -210,7 +132,11 @@ __global__ void __launch_bounds__(SX_WARPS * 32)
     WarpScratch *ws = wsa + warp;
     const int hi = L - 1 - Tp;
     const int t1 = min(hi + 1, (rb + 1) * TB);
-    for (int t = rb * TB + warp; t < t1; t += SX_WARPS) sweep_row<CH, HEAD1>(xs, t, hi, E_max, tau, Tp, mu, ws, m);
+    const unsigned keep = bitonic_keep_min_bits();
+    FallbackCount fc;
+    for (int t = rb * TB + warp; t < t1; t += SX_WARPS)
+        sweep_row<CH, HEAD1>(xs, t, hi, E_max, tau, Tp, mu, ws, m, keep, fc);
+    fc.flush(stats);
 #pragma unroll
     for (int j = 0; j < 5; ++j) red[(warp * 32 + lane) * 5 + j] = m[j];
     __syncthreads();
@@ -336,7 +262,7 @@ __device__ __forceinline__ void long_chunk(const float *xs, int L, int t, int hi
 }
 
 __device__ void sweep_long_row(const float *xs, int L, int t, int hi, int E_max, int tau, int Tp,
-                               float mu, LongScratch *sc, float (&m)[5]) {
+                               float mu, LongScratch *sc, float (&m)[5], FallbackCount &fc) {
     const int lane = lane_id();
     WarpScratch *ws = &sc->ws;
     // last E for which t is a point of P_E with enough points
@@ -362,6 +288,7 @@ __device__ void sweep_long_row(const float *xs, int L, int t, int hi, int E_max,
         const bool deg = __shfl_sync(FULL, degen, E - 1) != 0;
         const float edge = deg ? 0.f : band_edge(key_s(list[K - 1]), E);
         if (deg) {
+            fc.add(KNN_USED_BAND | KNN_USED_BRUTE);
             brute_fp64(xs, t, lo, hi, E, tau, ws, K);
             if (lane < K) {
                 u_out = ws->sel_u[lane];
@@ -386,6 +313,7 @@ __device__ void sweep_long_row(const float *xs, int L, int t, int hi, int E_max,
             __syncwarp();
             const int c = ws->count;
             __syncwarp();
+            fc.add(c <= KNN_CAP ? KNN_USED_BAND : KNN_USED_BAND | KNN_USED_BRUTE);
             if (c <= KNN_CAP)
                 rank_band_fp64(xs, t, E, tau, ws, c, K);
             else
@@ -411,7 +339,7 @@ __device__ void sweep_long_row(const float *xs, int L, int t, int hi, int E_max,
 template <bool SMEM>
 __global__ void __launch_bounds__(SX_WARPS * 32)
     sweep_long_kernel(const float *__restrict__ X, int L, int E_max, int tau, int Tp, int TB,
-                      int nrb, double *__restrict__ partial) {
+                      int nrb, double *__restrict__ partial, unsigned long long *stats) {
     extern __shared__ __align__(16) uint8_t smem[];
     LongScratch *sca = reinterpret_cast<LongScratch *>(smem);
     float *red = reinterpret_cast<float *>(smem + SX_WARPS * sizeof(LongScratch));
@@ -436,8 +364,10 @@ __global__ void __launch_bounds__(SX_WARPS * 32)
     float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     const int hi = L - 1 - Tp;
     const int t1 = min(hi + 1, (rb + 1) * TB);
+    FallbackCount fc;
     for (int t = rb * TB + warp; t < t1; t += SX_WARPS)
-        sweep_long_row(xs, L, t, hi, E_max, tau, Tp, mu, sca + warp, m);
+        sweep_long_row(xs, L, t, hi, E_max, tau, Tp, mu, sca + warp, m, fc);
+    fc.flush(stats);
 #pragma unroll
     for (int j = 0; j < 5; ++j) red[(warp * 32 + lane) * 5 + j] = m[j];
     __syncthreads();
@@ -511,7 +441,7 @@ edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max,
         for (int c : CHs)
             if (c >= ch) { CH = c; break; }
         const size_t smem = fixed + sizeof(float) * 32 * CH;
-        void (*kern)(const float *, int, int, int, int, int, int, double *) = nullptr;
+        void (*kern)(const float *, int, int, int, int, int, int, double *, unsigned long long *) = nullptr;
         const bool head1 = (E_max - 1) * tau < 32;
         switch (CH) {
         case 8: kern = head1 ? sweep_kernel<8, true> : sweep_kernel<8, false>; break;
@@ -523,7 +453,8 @@ edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max,
         }
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         before_launch(ctx);
-        kern<<<grid, SX_WARPS * 32, smem, ctx->stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial);
+        kern<<<grid, SX_WARPS * 32, smem, ctx->stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial,
+                                                          diag_stats(ctx));
         st = after_launch(ctx, "sweep_kernel");
         if (st != EDM_OK) return st;
     } else {
@@ -535,8 +466,9 @@ edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max,
         auto kern = smem_series ? sweep_long_kernel<true> : sweep_long_kernel<false>;
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         before_launch(ctx);
-        kern<<<grid, SX_WARPS * 32, smem, ctx->stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial);
-        st = after_launch(ctx, "simplex_kernel");
+        kern<<<grid, SX_WARPS * 32, smem, ctx->stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial,
+                                                          diag_stats(ctx));
+        st = after_launch(ctx, "sweep_long_kernel");
         if (st != EDM_OK) return st;
     }
     before_launch(ctx);
@@ -597,6 +529,8 @@ extern "C" edm_status edm_simplex_optimal_E_noalloc(const float *X, int N, int L
     int nrb = (L + TB - 1) / TB;
     const size_t per_block = static_cast<size_t>(E_max) * 5;
     if (static_cast<size_t>(N) * nrb * per_block > NOALLOC_SCRATCH_DOUBLES) {
+        // fewer, longer row blocks (never needed on a 152-SM GPU: there the
+        // split above always fits whenever N * E_max is within capacity)
         TB = L;
         nrb = 1;
     }
@@ -604,19 +538,22 @@ extern "C" edm_status edm_simplex_optimal_E_noalloc(const float *X, int N, int L
         return EDM_ERR_INVALID_ARG;  // N * E_max above the scratch capacity
     double *partial = nullptr;
     if (noalloc_scratch(device, &partial) != cudaSuccess) return EDM_ERR_CUDA;
+    // an error left pending by some earlier call is not this call's to report
+    // or to clear
+    if (cudaPeekAtLastError() != cudaSuccess) return EDM_ERR_CUDA;
 
-    const size_t fixed = SX_WARPS * sizeof(WarpScratch) + SX_WARPS * 32 * 5 * sizeof(float) +
-                         SX_WARPS * sizeof(double);
     dim3 grid(N, nrb);
     const int ch = (L + 31) / 32;
     if (ch <= 64) {
+        const size_t fixed = SX_WARPS * sizeof(WarpScratch) + SX_WARPS * 32 * 5 * sizeof(float) +
+                             SX_WARPS * sizeof(double);
         const int CHs[] = {8, 16, 24, 32, 48, 64};
         int CH = 64;
         for (int c : CHs)
             if (c >= ch) { CH = c; break; }
         const size_t smem = fixed + sizeof(float) * 32 * CH;
         const bool head1 = (E_max - 1) * tau < 32;
-        void (*kern)(const float *, int, int, int, int, int, int, double *) = nullptr;
+        void (*kern)(const float *, int, int, int, int, int, int, double *, unsigned long long *) = nullptr;
         switch (CH) {
         case 8: kern = head1 ? sweep_kernel<8, true> : sweep_kernel<8, false>; break;
         case 16: kern = head1 ? sweep_kernel<16, true> : sweep_kernel<16, false>; break;
@@ -628,16 +565,22 @@ extern "C" edm_status edm_simplex_optimal_E_noalloc(const float *X, int N, int L
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return EDM_ERR_CUDA;
-        kern<<<grid, SX_WARPS * 32, smem, stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial);
+        kern<<<grid, SX_WARPS * 32, smem, stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial,
+                                                     nullptr);
     } else {
+        // long series: the chunked incremental sweep of the context path
+        const size_t lfixed = SX_WARPS * sizeof(LongScratch) + SX_WARPS * 32 * 5 * sizeof(float) +
+                              SX_WARPS * sizeof(double);
         const bool smem_series = sizeof(float) * static_cast<size_t>(L) <= SX_SERIES_SMEM_MAX;
-        const size_t smem = fixed + (smem_series ? align_up(sizeof(float) * L, 16) : 0);
-        auto kern = smem_series ? simplex_kernel<true> : simplex_kernel<false>;
+        const size_t smem = lfixed + (smem_series ? align_up(sizeof(float) * L, 16) : 0);
+        auto kern = smem_series ? sweep_long_kernel<true> : sweep_long_kernel<false>;
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
             return EDM_ERR_CUDA;
-        kern<<<grid, SX_WARPS * 32, smem, stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial);
+        kern<<<grid, SX_WARPS * 32, smem, stream>>>(X, L, E_max, tau, Tp_sel, TB, nrb, partial,
+                                                     nullptr);
     }
+    // no error was pending before the launch, so one now is this call's
     if (cudaGetLastError() != cudaSuccess) return EDM_ERR_CUDA;
     simplex_finish_kernel<<<(N + 127) / 128, 128, 0, stream>>>(partial, N, L, E_max, tau, Tp_sel,
                                                                 nrb, E_opt, rho_E);

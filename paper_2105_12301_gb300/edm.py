@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(HERE, "libedm.so")
 EDM_OK = 0
 EDM_FP32 = 0
 EDM_BF16_TARGETS = 1
+EDM_FP16_TARGETS = 2
 EDM_E_MAX = 20
 EDM_K_MAX = 24
 EDM_L_MAX = 65535
@@ -80,6 +81,10 @@ def load():
     lib.edm_predict.argtypes = [vp, vp, ci, vp, ci, ci, vp, vp, ci, ci, vp]
     lib.edm_ccm_all_target_E.argtypes = [vp, vp, ci, vp, ci, ci, vp, ci, ci, ci, vp]
     lib.edm_ccm_all_host.argtypes = [vp, vp, ci, vp, ci, ci, vp, ci, ci, ci, vp, vp]
+    lib.edm_upload_series.argtypes = [vp, vp, ci, ci, vp]
+    lib.edm_ccm_rows.argtypes = [vp, vp, ci, ci, ci, ci, vp, ci, ci, ci, vp]
+    lib.edm_fallback_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64),
+                                        ctypes.POINTER(ctypes.c_uint64)]
     lib.edm_ccm_windows.argtypes = [vp, vp, ci, ci, ctypes.POINTER(ci), ci, ci, vp, ci, ci, ci, vp]
     lib.edm_profile_enable.argtypes = [vp, ci]
     lib.edm_profile_read.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
@@ -91,7 +96,8 @@ def load():
               "edm_profile_enable", "edm_profile_read", "edm_probe_smem_bandwidth",
               "edm_simplex_optimal_E_noalloc", "edm_ccm_window",
               "edm_simplex_optimal_E_batched", "edm_set_option", "edm_check_wait_timeout",
-              "edm_predict", "edm_ccm_all_target_E", "edm_ccm_all_host", "edm_ccm_windows"):
+              "edm_predict", "edm_ccm_all_target_E", "edm_ccm_all_host", "edm_ccm_windows",
+              "edm_upload_series", "edm_fallback_counts", "edm_ccm_rows"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -245,7 +251,9 @@ def _prec(precision):
         return EDM_FP32
     if precision in ("bf16", EDM_BF16_TARGETS):
         return EDM_BF16_TARGETS
-    raise ValueError("precision must be 'fp32' or 'bf16'")
+    if precision in ("fp16", EDM_FP16_TARGETS):
+        return EDM_FP16_TARGETS
+    raise ValueError("precision must be 'fp32', 'bf16' or 'fp16'")
 
 
 def edm_ccm_all(X_lib, Y_tgt, E_lib, tau=1, Tp=0, precision="fp32", out=None):
@@ -266,6 +274,24 @@ def edm_ccm_all(X_lib, Y_tgt, E_lib, tau=1, Tp=0, precision="fp32", out=None):
     ctx = _ctx(X_lib.device)
     _check(ctx, load().edm_ccm_all(ctx, _ptr(X_lib), N_lib, _ptr(Y_tgt), N_tgt, L, _ptr(E_lib),
                                    tau, Tp, _prec(precision), _ptr(rho)), "edm_ccm_all")
+    return rho
+
+
+def edm_ccm_rows(X, lib_begin, lib_end, E_lib, tau=1, Tp=0, precision="fp32", out=None):
+    """Rows lib_begin..lib_end-1 of the all-to-all rho matrix of the series X
+    [N][L] (libraries and targets alike): [lib_end-lib_begin][N] float32."""
+    _series(X, "X", 2)
+    N, L = X.shape
+    if not (0 <= lib_begin <= lib_end <= N):
+        raise ValueError("need 0 <= lib_begin <= lib_end <= N")
+    if E_lib.dtype != torch.int32 or not E_lib.is_cuda or E_lib.numel() != N:
+        raise TypeError("E_lib must be a CUDA int32 tensor of N entries")
+    rho = out if out is not None else torch.empty((lib_end - lib_begin, N), dtype=torch.float32,
+                                                  device=X.device)
+    ctx = _ctx(X.device)
+    _check(ctx, load().edm_ccm_rows(ctx, _ptr(X), N, L, lib_begin, lib_end,
+                                    _ptr(E_lib.contiguous()), tau, Tp, _prec(precision),
+                                    _ptr(rho)), "edm_ccm_rows")
     return rho
 
 
@@ -294,6 +320,36 @@ def edm_ccm_all_host(X_lib, Y_tgt, E_lib, out, out_host, tau=1, Tp=0, precision=
                                         _ptr(E_lib.contiguous()), tau, Tp, _prec(precision),
                                         _ptr(out), _ptr(out_host)), "edm_ccm_all_host")
     return out, out_host
+
+
+def edm_fallback_counts(device=None):
+    """(band_rows, brute_rows) counted since the previous call while the
+    option "diagnostics" is 1: query rows (per E) resolved in FP64 because a
+    candidate fell in the band around the k-th distance, and rows that needed
+    a full FP64 scan."""
+    dev = device if device is not None else torch.cuda.current_device()
+    ctx = _ctx(dev)
+    band, brute = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(ctx, load().edm_fallback_counts(ctx, ctypes.byref(band), ctypes.byref(brute)),
+           "edm_fallback_counts")
+    return int(band.value), int(brute.value)
+
+
+def edm_upload_series(X_host, out):
+    """Copy the page-locked host series X_host [N][L] (float32) into the CUDA
+    tensor `out` of the same shape, ordered on torch's current stream."""
+    if not isinstance(X_host, torch.Tensor) or X_host.is_cuda or not X_host.is_pinned():
+        raise TypeError("X_host must be a page-locked (pinned) CPU tensor")
+    if X_host.dtype != torch.float32 or X_host.dim() != 2 or not X_host.is_contiguous():
+        raise TypeError("X_host must be a contiguous float32 [N][L] tensor")
+    _series(out, "out", 2)
+    if tuple(out.shape) != tuple(X_host.shape):
+        raise ValueError("out must have the shape of X_host")
+    ctx = _ctx(out.device)
+    N, L = X_host.shape
+    _check(ctx, load().edm_upload_series(ctx, ctypes.c_void_p(X_host.data_ptr()), N, L,
+                                         _ptr(out)), "edm_upload_series")
+    return out
 
 
 def edm_ccm_all_target_E(X_lib, Y_tgt, E_tgt, tau=1, Tp=0, precision="fp32", out=None):

@@ -1,8 +1,12 @@
-"""Process-group helpers for running independent CCM problems on N GPUs.
+"""Process-group helpers for all-to-all CCM on N GPUs.
 
 Libraries are independent (section 2.1: the four steps run per library and
-target pair), so N ranks run N independent problems with no data exchange;
-the only collective is the max over ranks of the measured step time.
+target pair), so one problem splits into contiguous blocks of library rows,
+one block per rank, with every series replicated on every rank: a rank
+computes optimal E and the rho rows of its own libraries against all targets,
+with no exchange during the computation.  The only collectives are the max
+over ranks of the measured step time and an optional gather of the rho row
+blocks after the step.
 """
 import os
 
@@ -27,9 +31,27 @@ def init(backend=None):
     return rank, size
 
 
-def problem_seed(base_seed, rank):
-    """Seed of the problem a rank runs: rank 0 runs the reference workload."""
-    return base_seed if rank == 0 else base_seed + 7919 * rank
+def row_block(N, rank, size):
+    """The library rows [begin, end) of rank `rank` out of `size`: contiguous,
+    in rank order, covering 0..N-1 exactly once, sizes differing by at most 1."""
+    return rank * N // size, (rank + 1) * N // size
+
+
+def gather_row_blocks(block, N, device=None):
+    """All rho rows on every rank: block is this rank's [end-begin][M] rows
+    (row_block order); returns the [N][M] matrix.  Blocks are padded to the
+    largest block for the collective and trimmed after it."""
+    if not dist.is_initialized():
+        return block
+    size = dist.get_world_size()
+    M = block.shape[1]
+    rows = max(row_block(N, r, size)[1] - row_block(N, r, size)[0] for r in range(size))
+    pad = torch.zeros((rows, M), dtype=block.dtype, device=device if device is not None else block.device)
+    pad[: block.shape[0]] = block
+    parts = [torch.empty_like(pad) for _ in range(size)]
+    dist.all_gather(parts, pad)
+    return torch.cat([parts[r][: row_block(N, r, size)[1] - row_block(N, r, size)[0]]
+                      for r in range(size)])
 
 
 def barrier():

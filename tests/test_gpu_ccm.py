@@ -1,9 +1,12 @@
 """GPU parity of optimal-E selection and all-to-all CCM against the FP64 oracle.
 
-Tolerances: |rho_gpu - rho_oracle| <= 1e-5 with FP32 target storage and
-<= 1e-3 with BF16 target storage; the skills rho_E of the simplex sweep
-within 1e-5; E* equal to the oracle's unless the oracle's own skills of the
-two choices lie within 1e-5 of each other (a near-tie).
+Tolerances: |rho_gpu - rho_oracle| <= 1e-5 with FP32 target storage,
+<= 5e-4 with FP16 target storage, and with BF16 target storage <= 1e-3 when
+the library has at least 300 points and <= 2e-3 below that (BF16 keeps 8
+significant bits; the rounding of short targets alone moves rho by up to
+about 1.5e-3); the skills rho_E of the simplex sweep within 1e-5; E* equal
+to the oracle's unless the oracle's own skills of the two choices lie within
+1e-5 of each other (a near-tie).
 """
 import numpy as np
 import pytest
@@ -15,8 +18,17 @@ from paper_2105_12301_gb300 import edm, inputs
 pytestmark = pytest.mark.gpu
 
 TOL_FP32 = 1e-5
+TOL_FP16 = 5e-4
 TOL_BF16 = 1e-3
+TOL_BF16_SHORT = 2e-3      # BF16 with fewer than 300 library points
 TOL_RHO_E = 1e-5
+
+
+def tol16(precision, L):
+    """The bound of a 16-bit target storage at library length L."""
+    if precision == "fp16":
+        return TOL_FP16
+    return TOL_BF16 if L >= 300 else TOL_BF16_SHORT
 
 
 def gpu(x):
@@ -55,17 +67,55 @@ def test_logistic_16x200_optimal_E_and_full_rho_matrix():
     X = inputs.logistic_16x200()
     E = check_optimal_E(X, 10)
     check_ccm(X, X, E, 1, 0, "fp32", TOL_FP32)
-    check_ccm(X, X, E, 1, 0, "bf16", TOL_BF16)
+    check_ccm(X, X, E, 1, 0, "fp16", TOL_FP16)
+    check_ccm(X, X, E, 1, 0, "bf16", tol16("bf16", 200))
 
 
-def test_logistic_1000_sampled_libraries():
+def test_logistic_1000_full_matrix():
+    # 1,000 x 1,000 coupled logistic with noise: E* of every series against
+    # the oracle's, then all 10^6 rho values in every target storage
     X = inputs.logistic_noisy()
-    rows = np.arange(0, 1000, 71)
-    E = check_optimal_E(X[rows], 20)
-    E_all = np.full(1000, 3, np.int32)
-    E_all[rows] = E
-    check_ccm(X, X, E_all, 1, 0, "fp32", TOL_FP32, lib_rows=rows)
-    check_ccm(X, X, E_all, 1, 0, "bf16", TOL_BF16, lib_rows=rows)
+    E = check_optimal_E(X, 20)
+    ref = oracle.ccm_matrix(X, X, E, 1, 0)
+    ok = ~np.isnan(ref)
+    for prec, tol in (("fp32", TOL_FP32), ("fp16", TOL_FP16), ("bf16", TOL_BF16)):
+        rho = edm.edm_ccm_all(gpu(X), gpu(X), gpu(E), 1, 0, prec)
+        edm.edm_ctx_sync()
+        got = rho.cpu().numpy()
+        np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+        err = np.abs(got[ok] - ref[ok])
+        print("1000x1000 %s: max %.3g p99 %.3g over %d pairs"
+              % (prec, err.max(), np.percentile(err, 99), err.size))
+        assert err.max() <= tol, (prec, err.max())
+
+
+def test_library_length_windows_1000_sampled_pairs():
+    # 2,000 x 10,000 coupled logistic; E per library from the full-length
+    # simplex; CCM on the windows [0, L_lib) with 1,000 sampled (library,
+    # target) pairs per window checked against the oracle in every storage
+    X = inputs.logistic_long()
+    Xg = gpu(X)
+    E_full, _ = edm.edm_simplex_optimal_E(Xg, 20, 1, 1, with_rho=False)
+    E_np = E_full.cpu().numpy()
+    rng = np.random.default_rng(105)
+    lib_rows = np.sort(rng.choice(2000, 40, replace=False))
+    tgts = np.sort(rng.choice(2000, 25, replace=False))
+    for L_lib in (100, 300, 1000, 3000, 10000):
+        Xw = np.ascontiguousarray(X[:, :L_lib])
+        ref = oracle.ccm_matrix(Xw[lib_rows], Xw[tgts], E_np[lib_rows], 1, 0)
+        ok = ~np.isnan(ref)
+        assert ok.sum() >= 990
+        for prec in ("fp32", "fp16", "bf16"):
+            tol = TOL_FP32 if prec == "fp32" else tol16(prec, L_lib)
+            rho = edm.edm_ccm_window(Xg, 0, L_lib, E_full, 1, 0, prec)
+            edm.edm_ctx_sync()
+            got = rho.cpu().numpy()[np.ix_(lib_rows, tgts)]
+            del rho
+            np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+            err = np.abs(got[ok] - ref[ok])
+            print("window %d %s: max %.3g p99 %.3g over %d pairs"
+                  % (L_lib, prec, err.max(), np.percentile(err, 99), err.size))
+            assert err.max() <= tol, (L_lib, prec, err.max())
 
 
 @pytest.mark.parametrize("E", [1, 2, 7, 20])
@@ -80,7 +130,8 @@ def test_ragged_counts_tau_and_horizon():
     Y = inputs.coupled_logistic(70, 90, 9)        # 70 targets: ragged tiles
     E_lib = np.array([2, 5, 3], np.int32)
     check_ccm(X, Y, E_lib, 3, 2, "fp32", TOL_FP32)
-    check_ccm(X, Y, E_lib, 3, 2, "bf16", TOL_BF16)
+    check_ccm(X, Y, E_lib, 3, 2, "fp16", TOL_FP16)
+    check_ccm(X, Y, E_lib, 3, 2, "bf16", tol16("bf16", 90))
 
 
 def test_mixed_E_in_one_launch():
@@ -96,6 +147,7 @@ def test_half_width_target_tiles(L, N):
     X = inputs.coupled_logistic(N, L, 12 + L)
     E_lib = np.array([1, 2, 3, 4, 7] * 8, np.int32)[:N]
     check_ccm(X, X, E_lib, 1, 0, "fp32", TOL_FP32, lib_rows=[0, 13, N - 1])
+    check_ccm(X, X, E_lib, 1, 0, "fp16", TOL_FP16, lib_rows=[0, 13, N - 1])
     check_ccm(X, X, E_lib, 1, 0, "bf16", TOL_BF16, lib_rows=[0, 13, N - 1])
 
 
@@ -104,6 +156,7 @@ def test_long_series_gathers_from_global_memory():
     X = inputs.coupled_logistic(35, 3600, 13)
     E_lib = np.array([1, 2, 3, 4, 5] * 7, np.int32)
     check_ccm(X, X, E_lib, 1, 0, "fp32", TOL_FP32, lib_rows=[0, 13, 34])
+    check_ccm(X, X, E_lib, 1, 0, "fp16", TOL_FP16, lib_rows=[0, 13, 34])
     check_ccm(X, X, E_lib, 1, 0, "bf16", TOL_BF16, lib_rows=[0, 13, 34])
 
 
@@ -163,10 +216,12 @@ def test_full_size_calcium_workload_sampled():
     err = np.max(np.abs(rho[rows].cpu().numpy() - ref))
     assert err <= TOL_FP32, err
     del rho
-    rho = edm.edm_ccm_all(Xg, Xg, E_gpu, 1, 0, "bf16")
-    edm.edm_ctx_sync()
-    err = np.max(np.abs(rho[rows].cpu().numpy() - ref))
-    assert err <= TOL_BF16, err
+    for prec, tol in (("fp16", TOL_FP16), ("bf16", TOL_BF16)):
+        rho = edm.edm_ccm_all(Xg, Xg, E_gpu, 1, 0, prec)
+        edm.edm_ctx_sync()
+        err = np.max(np.abs(rho[rows].cpu().numpy() - ref))
+        del rho
+        assert err <= tol, (prec, err)
 
 
 @pytest.mark.parametrize("L,tau", [(2048, 1), (2049, 1), (1000, 2), (700, 3)])
@@ -251,7 +306,7 @@ def test_per_target_E_rule_matches_oracle():
     X = inputs.logistic_noisy(N=14, L=350)
     Y = inputs.coupled_logistic(11, 350, 5150)
     E_tgt = np.array([2, 1, 3, 2, 5, 20, 2, 1, 3, 7, 2], np.int32)
-    for prec, tol in (("fp32", TOL_FP32), ("bf16", TOL_BF16)):
+    for prec, tol in (("fp32", TOL_FP32), ("fp16", TOL_FP16), ("bf16", TOL_BF16)):
         rho = edm.edm_ccm_all_target_E(gpu(X), gpu(Y), gpu(E_tgt), 1, 0, prec)
         edm.edm_ctx_sync()
         rho = rho.cpu().numpy()
