@@ -537,6 +537,10 @@ def run_libsweep_workload(args):
     rho = torch.empty((N, N), dtype=torch.float32, device=dev)
     sizes = {}
     kernels = ("ccm_table_kernel", "lookup_kernel", "group_libs_kernel", "target_store_kernel")
+    smem_gbs = edm.edm_probe_smem_bandwidth(200.0, dev) / 1e9
+    l2_gbs = edm.edm_probe_l2_bandwidth(200.0, dev) / 1e9
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    E_np = E_full.cpu().numpy().astype(np.int64)
     for L_lib in (100, 300, 1000, 3000, 10000):
         for prec in ("fp32", "bf16"):
             def one():
@@ -548,14 +552,36 @@ def run_libsweep_workload(args):
             split = {k: edm.edm_profile_read(k, dev)[0] for k in kernels}
             edm.edm_profile_enable(False, dev)
             edm.edm_ctx_sync(dev)
-            sizes.setdefault(str(L_lib), {})[prec] = {"value": N * N / (ms / 1e3),
-                                                      "ms": ms, "kernel_ms": split}
+            # rooflines: the lookup's gathers (n k b bytes per pair) against
+            # shared memory while a tile fits it (<= 3,300 points), else
+            # against L2; the table builder against FP32 issue (E subs and
+            # FMAs plus a compare per candidate)
+            n_lib = np.maximum(L_lib - (E_np - 1) * TAU - TP, 0)
+            ok = n_lib >= E_np + 2
+            bpv = 4 if prec == "fp32" else 2
+            lk_bytes = float(np.sum((n_lib * (E_np + 1))[ok])) * N * bpv
+            tiled = L_lib <= 3300
+            peak = smem_gbs if tiled else l2_gbs
+            lk_ms = split["lookup_kernel"]
+            tb_ops = float(np.sum((n_lib * (n_lib - 1) * (2 * E_np + 1))[ok]))
+            tb_ms = split["ccm_table_kernel"]
+            alu_peak = n_sm * 128 * 2.07e9
+            sizes.setdefault(str(L_lib), {})[prec] = {
+                "value": N * N / (ms / 1e3), "ms": ms, "kernel_ms": split,
+                "lookup_roofline": {"bound": "smem" if tiled else "l2",
+                                    "achieved_gbs": lk_bytes / (lk_ms / 1e3) / 1e9 if lk_ms else None,
+                                    "peak_gbs": peak,
+                                    "frac": lk_bytes / (lk_ms / 1e3) / 1e9 / peak if lk_ms else None},
+                "table_roofline": {"bound": "alu", "lane_ops": tb_ops,
+                                   "frac": tb_ops / (tb_ms / 1e3) / alu_peak if tb_ms else None}}
             log("window %d %s %.1f ms %s" % (L_lib, prec, ms, split))
     out = {"metric": METRIC, "unit": UNIT, "higher_is_better": True, "n_gpus": 1,
            "data": "synthetic", "value": sizes["10000"]["fp32"]["value"],
            "config": {"workload": "library-length sweep, %d coupled-logistic series x %d steps, "
                                   "windows [0, L_lib)" % (N, L), "pairs_per_size": N * N},
            "optimal_E_ms": ms_E, "per_library_size": sizes,
+           "peaks": {"smem_gather_gbs": smem_gbs, "l2_gather_gbs": l2_gbs,
+                     "fp32_issue_lane_ops_per_s": n_sm * 128 * 2.07e9},
            "E_opt_hist": np.bincount(E_full.cpu().numpy(), minlength=E_MAX + 1)[1:].tolist()}
     print(json.dumps(out), flush=True)
 
@@ -580,6 +606,24 @@ def run_paper_micro_workload(args):
         rows = X.shape[0] * (L - (E - 1) * TAU)
         knn[str(E)] = {"ms": ms, "rows_per_s": rows / (ms / 1e3)}
         log("knn E=%d %.1f ms" % (E, ms))
+    # the paper's two-kernel route (Algorithms 1-2: the n x n distance matrix
+    # written to memory, then per-row selection), same results, as a baseline
+    knn_mat = {}
+    for E in (1, 2, 4, 8, 12, 16, 20):
+        def one():
+            edm.edm_knn_materialized(Xg, E, TAU, 0, with_dist=True)
+        one()
+        edm.edm_profile_enable(True, dev)
+        ms = sync_time(one, dev, stream, 1)
+        split = {k: edm.edm_profile_read(k, dev)[0] for k in ("dmat_kernel", "knn_from_dmat_kernel")}
+        edm.edm_profile_enable(False, dev)
+        edm.edm_ctx_sync(dev)
+        rows = X.shape[0] * (L - (E - 1) * TAU)
+        n = L - (E - 1) * TAU
+        knn_mat[str(E)] = {"ms": ms, "rows_per_s": rows / (ms / 1e3), "kernel_ms": split,
+                           "matrix_bytes_written": 4.0 * n * n * X.shape[0],
+                           "fused_ms": knn[str(E)]["ms"]}
+        log("knn materialised E=%d %.1f ms %s" % (E, ms, split))
     Y = inputs.ar1_series(100000, L, 2105)
     log("generated targets %s" % (Y.shape,))
     Yg = torch.from_numpy(Y).to(dev)
@@ -605,7 +649,7 @@ def run_paper_micro_workload(args):
            "config": {"workload": "knn: 16 coupled-logistic series x 10,000 steps, E = 1..20, exact "
                                   "order; lookup: 10 libraries (E = 3) x 100,000 AR(1) targets x "
                                   "10,000 steps", "tau": TAU, "Tp": TP},
-           "knn": knn, "lookup": lookup}
+           "knn": knn, "knn_materialized": knn_mat, "lookup": lookup}
     print(json.dumps(out), flush=True)
 
 

@@ -130,6 +130,13 @@ edm_status edm_profile_read(edm_ctx *ctx, const char *kernel, double *total_ms,
  * pattern, one conflict-free wavefront per read) for about `ms` ms. */
 edm_status edm_probe_smem_bandwidth(edm_ctx *ctx, double ms, double *bytes_per_s);
 
+/* L2 gather bandwidth of this GPU in bytes/s, the roofline of the lookup
+ * when a target tile does not fit shared memory (series longer than about
+ * 3,300 points) and its gathers go to L2: warps read whole 128-byte rows of
+ * a 48 MB global buffer (resident in L2) at scattered row indexes for about
+ * `ms` ms.  Allocates and frees its buffer. */
+edm_status edm_probe_l2_bandwidth(edm_ctx *ctx, double ms, double *bytes_per_s);
+
 /* Failure-detection check (no counterpart in the paper).  Every wait inside
  * a libedm kernel is bounded: after its limit it records EDM_ERR_TIMEOUT in
  * the context, sets an abort word of its thread block so that the block's
@@ -157,6 +164,15 @@ edm_status edm_embed(edm_ctx *ctx, const float *x, int L, int E, int tau,
  * 2 <= L <= EDM_L_MAX, N >= 1. */
 edm_status edm_knn(edm_ctx *ctx, const float *X, int N, int L, int E, int tau,
                    int Tp, int k, int32_t *idx, float *dist);
+
+/* edm_knn computed the way of the paper's Algorithms 1 and 2, as a measured
+ * baseline for the fused kernels (no new capability): for each series, one
+ * kernel writes the full n x n matrix of FP32 squared distances to device
+ * memory (a context workspace of 4 n^2 bytes), then a second kernel selects
+ * every row's k nearest from it, with the same exact FP64 ordering step.
+ * Arguments and results as for edm_knn; the results are identical. */
+edm_status edm_knn_materialized(edm_ctx *ctx, const float *X, int N, int L, int E, int tau,
+                                int Tp, int k, int32_t *idx, float *dist);
 
 /* Optimal embedding dimension per series (named in section 3.3; the method
  * is leave-one-out simplex projection of the series onto itself at horizon

@@ -550,6 +550,12 @@ edm_status edm_probe_smem_bandwidth(edm_ctx *ctx, double ms, double *bytes_per_s
     return launch_smem_probe(ctx, ms, bytes_per_s);
 }
 
+edm_status edm_probe_l2_bandwidth(edm_ctx *ctx, double ms, double *bytes_per_s) {
+    if (!ctx || !bytes_per_s || !(ms > 0.0)) return EDM_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    return launch_l2_probe(ctx, ms, bytes_per_s);
+}
+
 uint64_t edm_kernel_launches(edm_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
 edm_status edm_check_wait_timeout(edm_ctx *ctx, int ms) {
@@ -581,6 +587,20 @@ edm_status edm_knn(edm_ctx *ctx, const float *X, int N, int L, int E, int tau, i
                          n);
     DeviceGuard g(ctx->device);
     return launch_knn(ctx, X, N, L, E, tau, Tp, k, idx, dist);
+}
+
+edm_status edm_knn_materialized(edm_ctx *ctx, const float *X, int N, int L, int E, int tau,
+                                int Tp, int k, int32_t *idx, float *dist) {
+    if (!ctx) return EDM_ERR_INVALID_ARG;
+    if (!X || !idx || N < 1 || !series_len_ok(L) || E < 1 || E > EDM_E_MAX || tau < 1 ||
+        Tp < 0 || k < 1 || k > EDM_K_MAX)
+        return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_knn_materialized: bad arguments");
+    const long long n = static_cast<long long>(L) - static_cast<long long>(E - 1) * tau - Tp;
+    if (n < 2 || k > n - 1)
+        return set_error(ctx, EDM_ERR_INVALID_ARG,
+                         "edm_knn_materialized: k=%d needs more than %lld points", k, n);
+    DeviceGuard g(ctx->device);
+    return launch_knn_materialized(ctx, X, N, L, E, tau, Tp, k, idx, dist);
 }
 
 edm_status edm_simplex_optimal_E(edm_ctx *ctx, const float *X, int N, int L, int E_max, int tau,

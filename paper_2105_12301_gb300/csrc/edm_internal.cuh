@@ -142,6 +142,8 @@ edm_status launch_group_libs(edm_ctx *ctx, const int32_t *E_lib, int E_uniform, 
 edm_status launch_embed(edm_ctx *ctx, const float *x, int L, int E, int tau, float *out);
 edm_status launch_knn(edm_ctx *ctx, const float *X, int N, int L, int E, int tau, int Tp,
                       int k, int32_t *idx, float *dist);
+edm_status launch_knn_materialized(edm_ctx *ctx, const float *X, int N, int L, int E, int tau,
+                                   int Tp, int k, int32_t *idx, float *dist);
 // X: library series with row stride ld (>= L) floats; the libraries are
 // those of the groups g (indexes into X), tables laid out as described at
 // CcmGroups.
@@ -176,6 +178,7 @@ edm_status launch_predict(edm_ctx *ctx, const float *Y, long long ld_tgt, int N_
                           const int32_t *tgt_of, int L, int tau, int Tp, const CcmGroups &g,
                           const uint8_t *tables, int lib0, float *pred, long long ld_pred);
 edm_status launch_smem_probe(edm_ctx *ctx, double ms, double *bytes_per_s);
+edm_status launch_l2_probe(edm_ctx *ctx, double ms, double *bytes_per_s);
 edm_status launch_wait_check(edm_ctx *ctx, int ms);
 size_t simplex_workspace_bytes(edm_ctx *ctx, int N, int L, int E_max);
 // Autotuner bucket of a lookup launch.
@@ -276,6 +279,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
+// As mbar_try_wait, but the thread may be suspended in hardware for up to
+// `hint_ns` nanoseconds while the phase is incomplete (it resumes as soon as
+// the phase completes), instead of spinning on the barrier.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity,
+                                                    uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ uint64_t global_timer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -290,16 +309,20 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
 // Once the abort word is set, every later wait of the CTA that passes it
 // returns false at once instead of spinning for its own limit, so a CTA
 // whose pipeline broke ends within about one limit.
+// While waiting the thread sleeps in try_wait (up to 20 us a try, woken
+// when the phase completes) rather than spinning, so a waiting warp leaves
+// the issue slots to the warps that work; the timer is read once every 8
+// tries.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *flags,
                                                   volatile int *abort,
                                                   uint64_t limit_ns = 2000000000ull) {
     if (mbar_try_wait(bar, parity)) return true;
     if (abort && *abort) return false;
     const uint64_t t0 = global_timer_ns();
-    for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
+    for (unsigned tries = 1;; ++tries) {
+        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
         if (abort && *abort) return false;
-        if (global_timer_ns() - t0 > limit_ns) {
+        if ((tries & 7u) == 0 && global_timer_ns() - t0 > limit_ns) {
             set_flag(flags, EDMF_TIMEOUT);
             if (abort) *abort = 1;
             return false;

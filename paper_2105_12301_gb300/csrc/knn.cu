@@ -277,9 +277,15 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
 //   KNN_ORDERED (R = K+KNN_MARGIN): the exact FP64 order (s64, u), d the
 //     FP64 square root rounded to float.
 // On return lane r < K holds the r-th neighbour and its distance.
+//
+// drow (optional): the row's FP32 squared distances already materialised in
+// memory, drow[u - lo] for u in lo..hi (the value at t itself is ignored);
+// they are read instead of computed and must equal the values computed here
+// (same operations, same order), which the FP64 band step relies on.
 template <int MODE>
 __device__ int knn_row_chunked(const float *xs, int L, int t, int lo, int hi, int E, int tau,
-                               int K, TableLongScratch *sc, int &u_out, float &d_out) {
+                               int K, TableLongScratch *sc, int &u_out, float &d_out,
+                               const float *drow = nullptr) {
     const int lane = lane_id();
     WarpScratch *ws = &sc->ws;
     uint64_t *list = sc->list;
@@ -289,7 +295,13 @@ __device__ int knn_row_chunked(const float *xs, int L, int t, int lo, int hi, in
     bool deg = false;
     for (int c0 = 0; c0 <= hi; c0 += 32 * TL_CH) {
         float s[TL_CH];
-        if (c0 >= lo && c0 + 32 * TL_CH - 1 <= hi) {
+        if (drow) {
+#pragma unroll
+            for (int j = 0; j < TL_CH; ++j) {
+                const int u = c0 + lane + 32 * j;
+                s[j] = (u >= lo && u <= hi && u != t) ? __ldg(drow + (u - lo)) : EDM_INF;
+            }
+        } else if (c0 >= lo && c0 + 32 * TL_CH - 1 <= hi) {
             // every candidate is a point of P: no clamp, only t itself is out
             const float *xl = xs + (c0 + lane);
 #pragma unroll
@@ -481,6 +493,111 @@ __global__ void __launch_bounds__(KNN_WARPS * 32)
         }
     }
     fc.flush(stats);
+}
+
+// ---------------------------------------- materialised distances (baseline)
+//
+// The paper's two-kernel kNN (Algorithm 1 writes the n x n distance matrix
+// to memory, Algorithm 2 selects each row's k nearest from it), kept as a
+// measured baseline for the fused kernels above.  dmat_kernel writes the FP32
+// squared distances D[i][j] = s(lo+i, lo+j) of one series with the
+// operations of dist32 in the same order; knn_from_dmat_kernel runs one warp
+// per row through knn_row_chunked reading D instead of computing it, with the
+// same FP64 band step, so the output equals edm_knn's.
+constexpr int DM_TILE = 64;  // rows and columns of a dmat_kernel tile
+
+__global__ void __launch_bounds__(256)
+    dmat_kernel(const float *__restrict__ x, int lo, int n, int E, int tau,
+                float *__restrict__ D) {
+    // rows i0..i0+63 and columns j0..j0+63 need x[lo + i - l tau] for l < E
+    extern __shared__ __align__(16) float seg[];  // [2][64 + (E-1) tau]
+    const int span = DM_TILE + (E - 1) * tau;
+    float *ra = seg, *ca = seg + span;
+    const int i0 = blockIdx.y * DM_TILE, j0 = blockIdx.x * DM_TILE;
+    // ra[k] = x[lo + i0 - (E-1) tau + k], likewise for the columns
+    for (int k = threadIdx.x; k < span; k += blockDim.x) {
+        const int ti = lo + i0 - (E - 1) * tau + k, tj = lo + j0 - (E - 1) * tau + k;
+        ra[k] = (ti >= 0 && ti < lo + n) ? x[ti] : 0.f;
+        ca[k] = (tj >= 0 && tj < lo + n) ? x[tj] : 0.f;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 64 columns x 4 row groups
+    const int off = (E - 1) * tau;
+    float acc[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) acc[r] = 0.f;
+    for (int l = 0; l < E; ++l) {
+        const float b = ca[off + tx - l * tau];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const float d = __fsub_rn(ra[off + ty + 4 * r - l * tau], b);
+            acc[r] = __fmaf_rn(d, d, acc[r]);
+        }
+    }
+    const int j = j0 + tx;
+    if (j >= n) return;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int i = i0 + ty + 4 * r;
+        if (i < n) D[static_cast<size_t>(i) * n + j] = acc[r];
+    }
+}
+
+template <bool SMEM>
+__global__ void __launch_bounds__(KNN_WARPS * 32)
+    knn_from_dmat_kernel(const float *__restrict__ x, const float *__restrict__ D, int L, int E,
+                         int tau, int Tp, int K, int RB, int32_t *__restrict__ idx,
+                         float *__restrict__ dist) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    TableLongScratch *sca = reinterpret_cast<TableLongScratch *>(smem);
+    float *xs_s = reinterpret_cast<float *>(smem + KNN_WARPS * sizeof(TableLongScratch));
+    const float *xs = stage_series<SMEM>(x, L, xs_s);
+    const int lo = (E - 1) * tau, hi = L - 1 - Tp, n = hi - lo + 1;
+    const int r0 = blockIdx.x * RB, r1 = min(n, r0 + RB);
+    const int warp = threadIdx.x >> 5, lane = lane_id();
+    TableLongScratch *sc = sca + warp;
+    for (int i = r0 + warp; i < r1; i += KNN_WARPS) {
+        int u = 0;
+        float d = 0.f;
+        knn_row_chunked<KNN_ORDERED>(xs, L, lo + i, lo, hi, E, tau, K, sc, u, d,
+                                     D + static_cast<size_t>(i) * n);
+        if (lane < K) {
+            idx[static_cast<size_t>(i) * K + lane] = u;
+            if (dist) dist[static_cast<size_t>(i) * K + lane] = d;
+        }
+    }
+}
+
+edm_status launch_knn_materialized(edm_ctx *ctx, const float *X, int N, int L, int E, int tau,
+                                   int Tp, int k, int32_t *idx, float *dist) {
+    const int lo = (E - 1) * tau, n = L - lo - Tp;
+    edm_status st = ws_reserve(ctx, sizeof(float) * static_cast<size_t>(n) * n);
+    if (st != EDM_OK) return st;
+    float *D = static_cast<float *>(ctx->ws);
+    const int tiles = (n + DM_TILE - 1) / DM_TILE;
+    const size_t seg = 2 * sizeof(float) * (DM_TILE + (E - 1) * tau);
+    const int RB = rows_per_cta(ctx, 1, n);
+    const bool smem_series = sizeof(float) * static_cast<size_t>(L) <= SERIES_SMEM_MAX;
+    const size_t smem = KNN_WARPS * sizeof(TableLongScratch) +
+                        (smem_series ? align_up(sizeof(float) * L, 16) : 0);
+    auto sel = smem_series ? knn_from_dmat_kernel<true> : knn_from_dmat_kernel<false>;
+    cudaFuncSetAttribute(sel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(dmat_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seg);
+    // one series at a time: its matrix is the workspace
+    for (int sidx = 0; sidx < N; ++sidx) {
+        const float *x = X + static_cast<size_t>(sidx) * L;
+        before_launch(ctx);
+        dmat_kernel<<<dim3(tiles, tiles), 256, seg, ctx->stream>>>(x, lo, n, E, tau, D);
+        st = after_launch(ctx, "dmat_kernel");
+        if (st != EDM_OK) return st;
+        before_launch(ctx);
+        sel<<<(n + RB - 1) / RB, KNN_WARPS * 32, smem, ctx->stream>>>(
+            x, D, L, E, tau, Tp, k, RB, idx + static_cast<size_t>(sidx) * n * k,
+            dist ? dist + static_cast<size_t>(sidx) * n * k : nullptr);
+        st = after_launch(ctx, "knn_from_dmat_kernel");
+        if (st != EDM_OK) return st;
+    }
+    return EDM_OK;
 }
 
 size_t ccm_slot_bytes(int L, int tau, int Tp) {

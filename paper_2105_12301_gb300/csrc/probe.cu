@@ -72,6 +72,82 @@ edm_status launch_smem_probe(edm_ctx *ctx, double ms, double *bytes_per_s) {
     return st;
 }
 
+// L2 gather bandwidth: the access pattern of the lookup when the target tile
+// stays in global memory (series longer than a shared-memory tile allows):
+// every warp reads whole 128-byte rows (lane l reads word l) of a global
+// buffer at scattered row indexes, through the read-only path.  The buffer
+// (PL2_ROWS rows, 48 MB) fits the L2 cache but not L1, so after the first
+// pass every read is an L2 hit.
+constexpr int PL2_ROWS = 3 << 17;   // 393,216 rows of 128 B = 48 MB
+constexpr int PL2_UNROLL = 16;
+
+__global__ void __launch_bounds__(PR_WARPS * 32) l2_probe_kernel(const float *__restrict__ buf,
+                                                                 int iters, float *sink) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // a per-warp linear congruential walk over the rows (row < PL2_ROWS)
+    uint32_t r = 2654435761u * static_cast<uint32_t>(gw + 1);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < PL2_UNROLL; j += 4) {
+            r = r * 1664525u + 1013904223u;
+            a0 += __ldg(buf + static_cast<size_t>((r >> 8) % PL2_ROWS) * 32 + lane);
+            r = r * 1664525u + 1013904223u;
+            a1 += __ldg(buf + static_cast<size_t>((r >> 8) % PL2_ROWS) * 32 + lane);
+            r = r * 1664525u + 1013904223u;
+            a2 += __ldg(buf + static_cast<size_t>((r >> 8) % PL2_ROWS) * 32 + lane);
+            r = r * 1664525u + 1013904223u;
+            a3 += __ldg(buf + static_cast<size_t>((r >> 8) % PL2_ROWS) * 32 + lane);
+        }
+    }
+    const float s = a0 + a1 + a2 + a3;
+    if (s == -1.f) sink[blockIdx.x] = s;  // never true; keeps the loads alive
+}
+
+edm_status launch_l2_probe(edm_ctx *ctx, double ms, double *bytes_per_s) {
+    float *buf = nullptr, *sink = nullptr;
+    const size_t bytes = static_cast<size_t>(PL2_ROWS) * 128;
+    edm_status st = cuda_check(ctx, cudaMalloc(&buf, bytes), "l2 probe");
+    if (st != EDM_OK) return st;
+    st = cuda_check(ctx, cudaMalloc(&sink, sizeof(float) * 8 * ctx->num_sms), "l2 probe");
+    if (st != EDM_OK) {
+        cudaFree(buf);
+        return st;
+    }
+    cudaMemsetAsync(buf, 0, bytes, ctx->stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks = 4 * ctx->num_sms;  // 64 warps per SM
+    int iters = 16;
+    double got = 0.0;
+    before_launch(ctx);
+    l2_probe_kernel<<<blocks, PR_WARPS * 32, 0, ctx->stream>>>(buf, iters, sink);  // warm L2
+    st = after_launch(ctx, "l2_probe_kernel");
+    for (int attempt = 0; st == EDM_OK && attempt < 6; ++attempt) {
+        cudaEventRecord(e0, ctx->stream);
+        before_launch(ctx);
+        l2_probe_kernel<<<blocks, PR_WARPS * 32, 0, ctx->stream>>>(buf, iters, sink);
+        st = after_launch(ctx, "l2_probe_kernel");
+        if (st != EDM_OK) break;
+        cudaEventRecord(e1, ctx->stream);
+        st = cuda_check(ctx, cudaEventSynchronize(e1), "l2 probe sync");
+        if (st != EDM_OK) break;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        got = static_cast<double>(blocks) * PR_WARPS * iters * PL2_UNROLL * 128.0 / (t * 1e-3);
+        if (t >= 0.5 * ms) break;
+        iters = static_cast<int>(std::min<double>(1 << 22, iters * std::max(2.0, ms / std::max(t, 0.01f))));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    cudaFree(buf);
+    *bytes_per_s = got;
+    return st;
+}
+
 // One thread waits, with the bounded wait every pipelined kernel of the
 // library uses, on an mbarrier that expects one arrival which never comes.
 // The wait gives up after `ms` milliseconds, raises the timeout flag and sets

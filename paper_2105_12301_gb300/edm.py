@@ -83,6 +83,7 @@ def load():
     lib.edm_ccm_all_host.argtypes = [vp, vp, ci, vp, ci, ci, vp, ci, ci, ci, vp, vp]
     lib.edm_upload_series.argtypes = [vp, vp, ci, ci, vp]
     lib.edm_ccm_rows.argtypes = [vp, vp, ci, ci, ci, ci, vp, ci, ci, ci, vp]
+    lib.edm_knn_materialized.argtypes = [vp, vp, ci, ci, ci, ci, ci, ci, vp, vp]
     lib.edm_fallback_counts.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.POINTER(ctypes.c_uint64)]
     lib.edm_ccm_windows.argtypes = [vp, vp, ci, ci, ctypes.POINTER(ci), ci, ci, vp, ci, ci, ci, vp]
@@ -91,13 +92,15 @@ def load():
                                      ctypes.POINTER(ci)]
     lib.edm_probe_smem_bandwidth.argtypes = [vp, ctypes.c_double,
                                              ctypes.POINTER(ctypes.c_double)]
+    lib.edm_probe_l2_bandwidth.argtypes = [vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
     for f in ("edm_create", "edm_destroy", "edm_set_stream", "edm_ctx_sync", "edm_embed",
               "edm_knn", "edm_simplex_optimal_E", "edm_ccm_all", "edm_ccm_batched",
               "edm_profile_enable", "edm_profile_read", "edm_probe_smem_bandwidth",
               "edm_simplex_optimal_E_noalloc", "edm_ccm_window",
               "edm_simplex_optimal_E_batched", "edm_set_option", "edm_check_wait_timeout",
               "edm_predict", "edm_ccm_all_target_E", "edm_ccm_all_host", "edm_ccm_windows",
-              "edm_upload_series", "edm_fallback_counts", "edm_ccm_rows"):
+              "edm_upload_series", "edm_fallback_counts", "edm_ccm_rows",
+              "edm_knn_materialized", "edm_probe_l2_bandwidth"):
         getattr(lib, f).restype = ci
     _lib = lib
     return lib
@@ -180,6 +183,17 @@ def edm_probe_smem_bandwidth(ms=200.0, device=None):
     return bw.value
 
 
+def edm_probe_l2_bandwidth(ms=200.0, device=None):
+    """Measured L2 gather bandwidth of the GPU (128-byte rows at scattered
+    indexes of an L2-resident buffer), bytes/s."""
+    dev = device if device is not None else torch.cuda.current_device()
+    ctx = _ctx(dev)
+    bw = ctypes.c_double()
+    _check(ctx, load().edm_probe_l2_bandwidth(ctx, float(ms), ctypes.byref(bw)),
+           "edm_probe_l2_bandwidth")
+    return bw.value
+
+
 def edm_check_wait_timeout(ms=50, device=None):
     """Enqueue a bounded device-side wait that nothing completes; the next
     edm_ctx_sync raises EdmError(EDM_ERR_TIMEOUT)."""
@@ -210,6 +224,21 @@ def edm_knn(X, E, tau=1, Tp=0, k=None, with_dist=True):
     ctx = _ctx(X.device)
     _check(ctx, load().edm_knn(ctx, _ptr(X), N, L, E, tau, Tp, k, _ptr(idx), _ptr(dist)),
            "edm_knn")
+    return idx, dist
+
+
+def edm_knn_materialized(X, E, tau=1, Tp=0, k=None, with_dist=True):
+    """edm_knn by the paper's two-kernel route (distance matrix written to
+    memory, then per-row selection); the same results, kept as a baseline."""
+    _series(X, "X", 2)
+    N, L = X.shape
+    k = E + 1 if k is None else k
+    n = L - (E - 1) * tau - Tp
+    idx = torch.empty((N, max(n, 0), k), dtype=torch.int32, device=X.device)
+    dist = torch.empty((N, max(n, 0), k), dtype=torch.float32, device=X.device) if with_dist else None
+    ctx = _ctx(X.device)
+    _check(ctx, load().edm_knn_materialized(ctx, _ptr(X), N, L, E, tau, Tp, k, _ptr(idx),
+                                            _ptr(dist)), "edm_knn_materialized")
     return idx, dist
 
 

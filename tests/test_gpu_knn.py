@@ -117,3 +117,25 @@ def test_knn_chunked_long_series_exact_order(E, tau, Tp, k):
         oi, od = oracle.knn_row(x, E, tau, Tp, t, k=k)
         np.testing.assert_array_equal(idx[t - lo], oi)
         np.testing.assert_array_equal(dist[t - lo], od.astype(np.float32))
+
+
+@pytest.mark.parametrize("L,E,tau,Tp", [(300, 1, 1, 0), (300, 3, 2, 1), (2100, 2, 1, 0),
+                                         (2100, 7, 1, 0)])
+def test_materialized_baseline_equals_fused_knn_and_oracle(L, E, tau, Tp):
+    # the paper's two-kernel route (distance matrix in memory, then per-row
+    # selection) gives exactly edm_knn's neighbours and distances, and the
+    # oracle's on sampled rows
+    X = inputs.coupled_logistic(3, L, 77 + L + E)
+    Xg = gpu(X)
+    i_f, d_f = edm.edm_knn(Xg, E, tau, Tp)
+    i_m, d_m = edm.edm_knn_materialized(Xg, E, tau, Tp)
+    edm.edm_ctx_sync()
+    torch.testing.assert_close(i_m, i_f, rtol=0, atol=0)
+    torch.testing.assert_close(d_m, d_f, rtol=0, atol=0)
+    i_m = i_m.cpu().numpy()
+    t0 = (E - 1) * tau
+    n = L - t0 - Tp
+    for s in range(3):
+        for i in (0, 1, n // 2, n - 1):
+            oi, _ = oracle.knn_row(X[s], E, tau, Tp, t0 + i)
+            np.testing.assert_array_equal(i_m[s, i], oi)
