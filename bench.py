@@ -467,9 +467,11 @@ T_START = time.perf_counter()
 
 def run_batched_workload(args):
     """256 independent all-to-all CCM problems of uneven N and L (optimal E,
-    then CCM), batched (graph-captured, concurrent streams) against the same
-    problems launched one after another on one stream.  Optimal E is timed
-    once per mode; the CCM step per mode and target precision."""
+    then CCM), in three modes: "batched" (optimal E through the work-queue
+    launches, CCM over concurrent streams, both graph-captured), "streams"
+    (every instance its own launches, spread over concurrent streams,
+    graph-captured) and "per_instance" (every instance's launches one after
+    another on one stream)."""
     from paper_2105_12301_gb300 import edm
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
@@ -494,12 +496,13 @@ def run_batched_workload(args):
                                   "in [32, 2048], L log-uniform in [200, 5000], noise 0.02",
                       "pairs_per_step": pairs, "E_range": [1, E_MAX], "tau": TAU, "Tp": TP,
                       "Tp_sel": TP_SEL}}
-    for mode, opts in (("batched", {"batch_graph": 1, "batch_streams": 8}),
-                       ("per_instance", {"batch_graph": 0, "batch_streams": 1})):
+    for mode, opts in (("batched", {"batch_graph": 1, "batch_streams": 8, "batch_queue": 1}),
+                       ("streams", {"batch_graph": 1, "batch_streams": 8, "batch_queue": 0}),
+                       ("per_instance", {"batch_graph": 0, "batch_streams": 1, "batch_queue": 0})):
         for k, v in opts.items():
             edm.edm_set_option(k, v, dev)
         opt_E()
-        ms_E = sync_time(opt_E, dev, stream, 1)
+        ms_E = sync_time(opt_E, dev, stream, max(1, args.steps))
         log("%s optimal E %.1f ms" % (mode, ms_E))
         rec = {"optimal_E_ms": ms_E}
         for prec in ("fp32", "bf16"):

@@ -345,10 +345,21 @@ typedef struct edm_instance {
 edm_status edm_ccm_batched(edm_ctx *ctx, const edm_instance *inst, int n_inst,
                            edm_precision prec);
 
-/* Optimal E (as edm_simplex_optimal_E) of every series of every instance,
- * batched like edm_ccm_batched.  Only X, N, L and tau of each descriptor are
- * used; E_out is a HOST array of n_inst DEVICE pointers, E_out[i] [N_i]
- * int32. */
+/* Optimal E (as edm_simplex_optimal_E) of every series of every instance.
+ * Only X, N, L and tau of each descriptor are used; E_out is a HOST array of
+ * n_inst DEVICE pointers, E_out[i] [N_i] int32.
+ * Execution (no counterpart in the paper): by default every instance's work
+ * items -- (series, block of query times) -- go into one device work queue
+ * per kind of sweep (the register-resident sweep of each candidate count,
+ * and the chunked sweep of series longer than 2,048 points); each kind with
+ * work gets one persistent launch whose thread blocks take items from the
+ * queue until it is empty, largest problems first, and one kernel then
+ * finishes every series.  The query times per work item are autotuned per
+ * kind (128, 256 or 512, timed on the first batch that needs the kind).  The
+ * sequence is captured once into a CUDA graph and replayed for the same
+ * batch.  Option "batch_queue" 0 (or an instance longer than 24,576 points)
+ * runs the instances as separate launches over concurrent streams instead,
+ * like edm_ccm_batched. */
 edm_status edm_simplex_optimal_E_batched(edm_ctx *ctx, const edm_instance *inst,
                                          int n_inst, int E_max, int Tp_sel,
                                          int32_t *const *E_out);
@@ -361,6 +372,7 @@ edm_status edm_simplex_optimal_E_batched(edm_ctx *ctx, const edm_instance *inst,
  *   "table_budget_mb"      >= 16  workspace for neighbour tables (2048)
  *   "autotune_reset"       1      forget the tuned values
  *   "diagnostics"          0/1    count FP64 band and brute-force rows (0)
+ *   "batch_queue"          0/1    batched optimal E through work queues (1)
  * Returns EDM_ERR_INVALID_ARG for an unknown name or value. */
 edm_status edm_set_option(edm_ctx *ctx, const char *name, long long value);
 

@@ -306,18 +306,21 @@ static edm_status run_batched(edm_ctx *ctx, int n, const std::vector<double> &wo
         if (st != EDM_OK) return set_error(ctx, st, "%s", sub->last_error);
     }
     auto enqueue = [&](cudaStream_t from) -> edm_status {
-        if (cudaEventRecord(ctx->ev_fork, from) != cudaSuccess)
-            return set_error(ctx, EDM_ERR_CUDA, "batch fork failed");
-        for (int s = 0; s < S; ++s) cudaStreamWaitEvent(ctx->subs[s]->stream, ctx->ev_fork, 0);
+        edm_status e = cuda_check(ctx, cudaEventRecord(ctx->ev_fork, from), "batch fork");
+        for (int s = 0; s < S && e == EDM_OK; ++s)
+            e = cuda_check(ctx, cudaStreamWaitEvent(ctx->subs[s]->stream, ctx->ev_fork, 0),
+                           "batch fork wait");
+        if (e != EDM_OK) return e;
         for (int i : order) {
-            edm_status e = fn(ctx->subs[assign[i]], i);
+            e = fn(ctx->subs[assign[i]], i);
             if (e != EDM_OK) return set_error(ctx, e, "instance %d: %s", i, ctx->subs[assign[i]]->last_error);
         }
-        for (int s = 0; s < S; ++s) {
-            cudaEventRecord(ctx->ev_join[s], ctx->subs[s]->stream);
-            cudaStreamWaitEvent(from, ctx->ev_join[s], 0);
+        for (int s = 0; s < S && e == EDM_OK; ++s) {
+            e = cuda_check(ctx, cudaEventRecord(ctx->ev_join[s], ctx->subs[s]->stream), "batch join");
+            if (e == EDM_OK)
+                e = cuda_check(ctx, cudaStreamWaitEvent(from, ctx->ev_join[s], 0), "batch join wait");
         }
-        return EDM_OK;
+        return e;
     };
     uint64_t before = 0;
     for (int s = 0; s < S; ++s) before += ctx->subs[s]->launches;
@@ -451,6 +454,7 @@ edm_status edm_destroy(edm_ctx *ctx) {
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_done) cudaEventDestroy(ctx->ev_done);
     if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->qgraph_exec) cudaGraphExecDestroy(ctx->qgraph_exec);
     if (ctx->origin) cudaStreamDestroy(ctx->origin);
     if (ctx->copy_stream) {
         cudaStreamSynchronize(ctx->copy_stream);
@@ -859,6 +863,12 @@ edm_status edm_simplex_optimal_E_batched(edm_ctx *ctx, const edm_instance *inst,
     }
     if (n_inst == 0) return EDM_OK;
     DeviceGuard g(ctx->device);
+    bool queue_ok = ctx->batch_queue;
+    for (int i = 0; i < n_inst && queue_ok; ++i) queue_ok = sweep_queue_ok(inst[i].L);
+    if (queue_ok) {
+        return launch_simplex_queue(ctx, inst, n_inst, E_max, Tp_sel, E_out, true,
+                                    ctx->batch_graph);
+    }
     std::vector<double> work(n_inst);
     std::vector<size_t> need(n_inst);
     uint64_t key = 1469598103934665603ull;
@@ -895,11 +905,14 @@ edm_status edm_set_option(edm_ctx *ctx, const char *name, long long value) {
         ctx->tune->clear();
     } else if (!strcmp(name, "diagnostics") && (value == 0 || value == 1)) {
         ctx->diag = value != 0;
+    } else if (!strcmp(name, "batch_queue") && (value == 0 || value == 1)) {
+        ctx->batch_queue = value != 0;
     } else {
         return set_error(ctx, EDM_ERR_INVALID_ARG, "edm_set_option: bad option %s=%lld", name,
                          value);
     }
     ctx->graph_key = 0;  // options change what a captured graph would hold
+    ctx->qgraph_key = 0;
     return EDM_OK;
 }
 

@@ -53,6 +53,10 @@ struct edm_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     uint64_t graph_key = 0;
     uint64_t graph_kernels = 0;  // kernels one replay of graph_exec launches
+    bool batch_queue = true;     // batched optimal E through the work queues
+    cudaGraphExec_t qgraph_exec = nullptr;  // the cached graph of the queues
+    uint64_t qgraph_key = 0;
+    uint64_t qgraph_kernels = 0;
 
     // copies of finished rho blocks to host memory (edm_ccm_all_host)
     cudaStream_t copy_stream = nullptr;
@@ -151,6 +155,13 @@ edm_status launch_ccm_tables(edm_ctx *ctx, const float *X, long long ld, int nli
                              int tau, int Tp, const CcmGroups &g, uint8_t *tables);
 edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max, int tau,
                           int Tp_sel, int32_t *E_opt, float *rho_E);
+// Optimal E of every series of every instance through one persistent
+// work-queue launch per kind of sweep (autotuned rows per work item when
+// `tune`), captured into a cached graph when `capture`.  Instances longer
+// than 24,576 points are not supported here (see sweep_queue_ok).
+edm_status launch_simplex_queue(edm_ctx *ctx, const edm_instance *inst, int n, int E_max,
+                                int Tp_sel, int32_t *const *E_out, bool tune, bool capture);
+inline bool sweep_queue_ok(int L) { return L <= 24576; }
 // Transposed, centred target tiles plus, per E = 1..EDM_E_MAX, the FP64 sums
 // of the stored values and of their squares over the observation window of
 // E (times (E-1)tau+Tp .. L-1): ysum / yysum [EDM_E_MAX][N_tgt].  mean_ws

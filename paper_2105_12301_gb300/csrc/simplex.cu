@@ -105,18 +105,20 @@ __device__ __forceinline__ void sweep_row(const float *xs, int t, int hi, int E_
     }
 }
 
-// One CTA per series (series staged in shared memory, zero-padded to 32*CH
-// points); warps take query times t = warp, warp + SX_WARPS, ...
+// One CTA-sized block of work: series `series` (staged in shared memory,
+// zero-padded to 32*CH points) and its query times rb*TB .. rb*TB+TB-1;
+// warps take query times t = warp, warp + SX_WARPS, ...  Writes the block's
+// FP64 partial moments and ends with a barrier, so the shared memory can be
+// reused for the next block.
 template <int CH, bool HEAD1>
-__global__ void __launch_bounds__(SX_WARPS * 32)
-    sweep_kernel(const float *__restrict__ X, int L, int E_max, int tau, int Tp, int TB, int nrb,
-                 double *__restrict__ partial, unsigned long long *stats) {
-    extern __shared__ __align__(16) uint8_t smem[];
+__device__ __forceinline__ void sweep_block(uint8_t *smem, const float *__restrict__ X, int L,
+                                            int E_max, int tau, int Tp, int TB, int nrb,
+                                            int series, int rb, double *__restrict__ partial,
+                                            unsigned long long *stats) {
     WarpScratch *wsa = reinterpret_cast<WarpScratch *>(smem);
     float *red = reinterpret_cast<float *>(smem + SX_WARPS * sizeof(WarpScratch));
     double *mu_s = reinterpret_cast<double *>(red + SX_WARPS * 32 * 5);
     float *xs = reinterpret_cast<float *>(mu_s + SX_WARPS);
-    const int series = blockIdx.x, rb = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const float *xg = X + static_cast<size_t>(series) * L;
     double acc = 0.0;
@@ -146,6 +148,17 @@ __global__ void __launch_bounds__(SX_WARPS * 32)
         for (int w = 0; w < SX_WARPS; ++w) sum += static_cast<double>(red[(w * 32 + e) * 5 + j]);
         partial[((static_cast<size_t>(series) * nrb + rb) * E_max + e) * 5 + j] = sum;
     }
+    __syncthreads();
+}
+
+// One CTA per (series, block of query times).
+template <int CH, bool HEAD1>
+__global__ void __launch_bounds__(SX_WARPS * 32)
+    sweep_kernel(const float *__restrict__ X, int L, int E_max, int tau, int Tp, int TB, int nrb,
+                 double *__restrict__ partial, unsigned long long *stats) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    sweep_block<CH, HEAD1>(smem, X, L, E_max, tau, Tp, TB, nrb, blockIdx.x, blockIdx.y, partial,
+                           stats);
 }
 
 // ---------------------------------------------------------------------------
@@ -337,15 +350,14 @@ __device__ void sweep_long_row(const float *xs, int L, int t, int hi, int E_max,
 }
 
 template <bool SMEM>
-__global__ void __launch_bounds__(SX_WARPS * 32)
-    sweep_long_kernel(const float *__restrict__ X, int L, int E_max, int tau, int Tp, int TB,
-                      int nrb, double *__restrict__ partial, unsigned long long *stats) {
-    extern __shared__ __align__(16) uint8_t smem[];
+__device__ __forceinline__ void sweep_long_block(uint8_t *smem, const float *__restrict__ X, int L,
+                                                 int E_max, int tau, int Tp, int TB, int nrb,
+                                                 int series, int rb, double *__restrict__ partial,
+                                                 unsigned long long *stats) {
     LongScratch *sca = reinterpret_cast<LongScratch *>(smem);
     float *red = reinterpret_cast<float *>(smem + SX_WARPS * sizeof(LongScratch));
     double *mu_s = reinterpret_cast<double *>(red + SX_WARPS * 32 * 5);
     float *xs_s = reinterpret_cast<float *>(mu_s + SX_WARPS);
-    const int series = blockIdx.x, rb = blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const float *xg = X + static_cast<size_t>(series) * L;
     double acc = 0.0;
@@ -377,14 +389,94 @@ __global__ void __launch_bounds__(SX_WARPS * 32)
         for (int w = 0; w < SX_WARPS; ++w) sum += static_cast<double>(red[(w * 32 + e) * 5 + j]);
         partial[((static_cast<size_t>(series) * nrb + rb) * E_max + e) * 5 + j] = sum;
     }
+    __syncthreads();
 }
 
-// One thread per series: sum the partials, rho per E, argmax.
-__global__ void simplex_finish_kernel(const double *__restrict__ partial, int N, int L, int E_max,
-                                      int tau, int Tp, int nrb, int32_t *__restrict__ E_opt,
-                                      float *__restrict__ rho_E) {
-    const int series = blockIdx.x * blockDim.x + threadIdx.x;
-    if (series >= N) return;
+template <bool SMEM>
+__global__ void __launch_bounds__(SX_WARPS * 32)
+    sweep_long_kernel(const float *__restrict__ X, int L, int E_max, int tau, int Tp, int TB,
+                      int nrb, double *__restrict__ partial, unsigned long long *stats) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    sweep_long_block<SMEM>(smem, X, L, E_max, tau, Tp, TB, nrb, blockIdx.x, blockIdx.y, partial,
+                           stats);
+}
+
+// ---------------------------------------------------------------------------
+// Batched optimal E as a work queue (many uneven problems in one launch per
+// kind of sweep).  A job is one problem; its work items are its (series,
+// block of TB query times) pairs, numbered from item0 in the queue of its
+// kind.  The launch is persistent: a grid sized to the resident CTAs takes
+// items from one device counter until the queue is empty, so problems of
+// every size share the GPU without a launch (and a tail) per problem.  Jobs
+// are queued largest first.
+
+struct SweepJob {
+    const float *X;       // [N][L]
+    double *partial;      // [N][nrb][E_max][5]
+    int32_t *E_opt;       // [N]
+    long long item0;      // first item of this job in its queue
+    int N, L, tau, TB, nrb;
+};
+
+// The job of queue item g: the last job whose item0 <= g (jobs ascending).
+__device__ __forceinline__ int job_of(const SweepJob *jobs, int njobs, long long g) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].item0 <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int CH, bool HEAD1>
+__global__ void __launch_bounds__(SX_WARPS * 32)
+    sweep_queue_kernel(const SweepJob *__restrict__ jobs, int njobs, long long nitems,
+                       unsigned long long *counter, int E_max, int Tp,
+                       unsigned long long *stats) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ long long item_s;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = static_cast<long long>(atomicAdd(counter, 1ull));
+        __syncthreads();
+        const long long g = item_s;
+        __syncthreads();
+        if (g >= nitems) break;
+        const SweepJob J = jobs[job_of(jobs, njobs, g)];
+        const long long local = g - J.item0;
+        sweep_block<CH, HEAD1>(smem, J.X, J.L, E_max, J.tau, Tp, J.TB, J.nrb,
+                               static_cast<int>(local / J.nrb), static_cast<int>(local % J.nrb),
+                               J.partial, stats);
+    }
+}
+
+__global__ void __launch_bounds__(SX_WARPS * 32)
+    sweep_long_queue_kernel(const SweepJob *__restrict__ jobs, int njobs, long long nitems,
+                            unsigned long long *counter, int E_max, int Tp,
+                            unsigned long long *stats) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ long long item_s;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = static_cast<long long>(atomicAdd(counter, 1ull));
+        __syncthreads();
+        const long long g = item_s;
+        __syncthreads();
+        if (g >= nitems) break;
+        const SweepJob J = jobs[job_of(jobs, njobs, g)];
+        const long long local = g - J.item0;
+        sweep_long_block<true>(smem, J.X, J.L, E_max, J.tau, Tp, J.TB, J.nrb,
+                               static_cast<int>(local / J.nrb), static_cast<int>(local % J.nrb),
+                               J.partial, stats);
+    }
+}
+
+// Sum the partials of one series, rho per E, argmax.
+__device__ __forceinline__ void finish_series(const double *__restrict__ partial, int series, int L,
+                                              int E_max, int tau, int Tp, int nrb,
+                                              int32_t *__restrict__ E_opt,
+                                              float *__restrict__ rho_E) {
     int best_E = 1;
     double best = 0.0;
     bool have = false;
@@ -406,6 +498,35 @@ __global__ void simplex_finish_kernel(const double *__restrict__ partial, int N,
         }
     }
     E_opt[series] = best_E;
+}
+
+// One thread per series.
+__global__ void simplex_finish_kernel(const double *__restrict__ partial, int N, int L, int E_max,
+                                      int tau, int Tp, int nrb, int32_t *__restrict__ E_opt,
+                                      float *__restrict__ rho_E) {
+    const int series = blockIdx.x * blockDim.x + threadIdx.x;
+    if (series >= N) return;
+    finish_series(partial, series, L, E_max, tau, Tp, nrb, E_opt, rho_E);
+}
+
+// One thread per series of every job of a batched run: jobs[i] covers the
+// global series series0[i] .. series0[i] + N - 1 (series0 ascending).
+__global__ void simplex_finish_jobs_kernel(const SweepJob *__restrict__ jobs,
+                                           const long long *__restrict__ series0, int njobs,
+                                           long long total, int E_max, int Tp) {
+    const long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (series0[mid] <= g)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const SweepJob J = jobs[lo];
+    finish_series(J.partial, static_cast<int>(g - series0[lo]), J.L, E_max, J.tau, Tp, J.nrb,
+                  J.E_opt, nullptr);
 }
 
 static void simplex_geometry(edm_ctx *ctx, int N, int L, int &TB, int &nrb) {
@@ -475,6 +596,306 @@ edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max,
     simplex_finish_kernel<<<(N + 127) / 128, 128, 0, ctx->stream>>>(partial, N, L, E_max, tau,
                                                                       Tp_sel, nrb, E_opt, rho_E);
     return after_launch(ctx, "simplex_finish_kernel");
+}
+
+// ---------------------------------------------------------------------------
+// Batched optimal E through the work queues.
+//
+// Kinds of sweep: the register-resident sweep for each slot count CH (8, 16,
+// 24, 32, 48, 64; HEAD1 when every lag offset is below 32) and the chunked
+// sweep for series longer than 2,048 points.  Each kind with jobs gets one
+// persistent launch; then one kernel finishes every series of every job.
+
+constexpr int SQ_KINDS = 13;   // 6 slot counts x HEAD1 or not, + the long sweep
+constexpr int SQ_LONG = 12;
+constexpr int SQ_CH[6] = {8, 16, 24, 32, 48, 64};
+
+static int sweep_kind(int L, int E_max, int tau) {
+    const int ch = (L + 31) / 32;
+    if (ch > 64) return SQ_LONG;
+    int c = 5;
+    for (int i = 0; i < 6; ++i)
+        if (SQ_CH[i] >= ch) { c = i; break; }
+    return 2 * c + ((E_max - 1) * tau < 32 ? 1 : 0);
+}
+
+using QueueKernel = void (*)(const SweepJob *, int, long long, unsigned long long *, int, int,
+                             unsigned long long *);
+
+static QueueKernel queue_kernel(int kind) {
+    switch (kind) {
+    case 0: return sweep_queue_kernel<8, false>;
+    case 1: return sweep_queue_kernel<8, true>;
+    case 2: return sweep_queue_kernel<16, false>;
+    case 3: return sweep_queue_kernel<16, true>;
+    case 4: return sweep_queue_kernel<24, false>;
+    case 5: return sweep_queue_kernel<24, true>;
+    case 6: return sweep_queue_kernel<32, false>;
+    case 7: return sweep_queue_kernel<32, true>;
+    case 8: return sweep_queue_kernel<48, false>;
+    case 9: return sweep_queue_kernel<48, true>;
+    case 10: return sweep_queue_kernel<64, false>;
+    case 11: return sweep_queue_kernel<64, true>;
+    default: return sweep_long_queue_kernel;
+    }
+}
+
+static size_t queue_smem(int kind, int L_max) {
+    const size_t red = SX_WARPS * 32 * 5 * sizeof(float) + SX_WARPS * sizeof(double);
+    if (kind == SQ_LONG) return SX_WARPS * sizeof(LongScratch) + red + align_up(sizeof(float) * L_max, 16);
+    return SX_WARPS * sizeof(WarpScratch) + red + sizeof(float) * 32 * SQ_CH[kind / 2];
+}
+
+// Rows per work item of a kind: the tuned value if any, else 256.
+static int queue_rows(edm_ctx *ctx, int kind) {
+    if (ctx->tune) {
+        auto it = ctx->tune->find(0x5157000000000000ull | static_cast<uint64_t>(kind));
+        if (it != ctx->tune->end()) return it->second;
+    }
+    return 256;
+}
+
+struct SweepQueuePlan {
+    int njobs = 0;
+    std::vector<int> kinds;                  // kinds with jobs
+    int job0[SQ_KINDS] = {}, njob[SQ_KINDS] = {};
+    long long items[SQ_KINDS] = {};
+    int L_max[SQ_KINDS] = {};
+    long long series_total = 0;
+    SweepJob *d_jobs = nullptr;
+    long long *d_series0 = nullptr;
+    unsigned long long *d_counters = nullptr;
+    size_t bytes = 0;                        // workspace used
+};
+
+// Lay the batch out in the context's workspace: the job descriptors (grouped
+// by kind, each kind's jobs largest first), their series offsets, one queue
+// counter per kind, then the partial moments of every job.  rows[kind] is the
+// query times per work item.  Copies the descriptors to the device (and
+// synchronises the stream): call before any capture.
+static edm_status plan_sweep_queue(edm_ctx *ctx, const edm_instance *inst, int n, int E_max,
+                                   int32_t *const *E_out, const int *rows, SweepQueuePlan &P) {
+    std::vector<int> order[SQ_KINDS];
+    for (int i = 0; i < n; ++i) order[sweep_kind(inst[i].L, E_max, inst[i].tau)].push_back(i);
+    std::vector<SweepJob> jobs;
+    std::vector<long long> series0;
+    size_t partial_doubles = 0;
+    P = SweepQueuePlan();
+    for (int k = 0; k < SQ_KINDS; ++k) {
+        auto &o = order[k];
+        if (o.empty()) continue;
+        std::stable_sort(o.begin(), o.end(), [&](int a, int b) {
+            return static_cast<double>(inst[a].N) * inst[a].L * inst[a].L >
+                   static_cast<double>(inst[b].N) * inst[b].L * inst[b].L;
+        });
+        P.kinds.push_back(k);
+        P.job0[k] = static_cast<int>(jobs.size());
+        P.njob[k] = static_cast<int>(o.size());
+        long long item = 0;
+        for (int i : o) {
+            const edm_instance &p = inst[i];
+            SweepJob J;
+            J.X = p.X;
+            J.N = p.N;
+            J.L = p.L;
+            J.tau = p.tau;
+            J.TB = std::min(std::max(rows[k], SX_WARPS), p.L);
+            J.nrb = (p.L + J.TB - 1) / J.TB;
+            J.E_opt = E_out[i];
+            J.item0 = item;
+            J.partial = reinterpret_cast<double *>(partial_doubles);  // offset for now
+            partial_doubles += static_cast<size_t>(p.N) * J.nrb * E_max * 5;
+            item += static_cast<long long>(p.N) * J.nrb;
+            P.L_max[k] = std::max(P.L_max[k], p.L);
+            jobs.push_back(J);
+            series0.push_back(P.series_total);
+            P.series_total += p.N;
+        }
+        P.items[k] = item;
+    }
+    P.njobs = static_cast<int>(jobs.size());
+    const size_t jb = align_up(sizeof(SweepJob) * jobs.size(), 256);
+    const size_t sb = align_up(sizeof(long long) * series0.size(), 256);
+    const size_t cb = align_up(sizeof(unsigned long long) * SQ_KINDS, 256);
+    P.bytes = jb + sb + cb + sizeof(double) * partial_doubles;
+    edm_status st = ws_reserve(ctx, P.bytes);
+    if (st != EDM_OK) return st;
+    uint8_t *base = static_cast<uint8_t *>(ctx->ws);
+    P.d_jobs = reinterpret_cast<SweepJob *>(base);
+    P.d_series0 = reinterpret_cast<long long *>(base + jb);
+    P.d_counters = reinterpret_cast<unsigned long long *>(base + jb + sb);
+    double *partial = reinterpret_cast<double *>(base + jb + sb + cb);
+    for (auto &J : jobs) J.partial = partial + reinterpret_cast<size_t>(J.partial);
+    st = cuda_check(ctx, cudaMemcpyAsync(P.d_jobs, jobs.data(), sizeof(SweepJob) * jobs.size(),
+                                         cudaMemcpyHostToDevice, ctx->stream), "queue jobs");
+    if (st == EDM_OK)
+        st = cuda_check(ctx, cudaMemcpyAsync(P.d_series0, series0.data(),
+                                             sizeof(long long) * series0.size(),
+                                             cudaMemcpyHostToDevice, ctx->stream), "queue jobs");
+    // the host vectors must outlive the copies
+    if (st == EDM_OK) st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "queue jobs");
+    return st;
+}
+
+// Enqueue the planned batch on `stream`: reset the counters, one persistent
+// launch per kind (times in ms per kind when `ms` is given, which
+// synchronises), then the finish of every series.
+static edm_status enqueue_sweep_queue(edm_ctx *ctx, const SweepQueuePlan &P, int E_max, int Tp_sel,
+                                      cudaStream_t stream, float *ms) {
+    edm_status st = cuda_check(ctx, cudaMemsetAsync(P.d_counters, 0,
+                                                    sizeof(unsigned long long) * SQ_KINDS, stream),
+                               "queue counters");
+    if (st != EDM_OK) return st;
+    for (int k : P.kinds) {
+        QueueKernel kern = queue_kernel(k);
+        const size_t smem = queue_smem(k, P.L_max[k]);
+        st = cuda_check(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  static_cast<int>(smem)), "queue attribute");
+        if (st != EDM_OK) return st;
+        int per_sm = 0;
+        st = cuda_check(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern,
+                                                                           SX_WARPS * 32, smem),
+                        "queue occupancy");
+        if (st != EDM_OK) return st;
+        const long long want = static_cast<long long>(std::max(per_sm, 1)) * ctx->num_sms;
+        const int grid = static_cast<int>(std::min<long long>(want, P.items[k]));
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (ms) {
+            st = cuda_check(ctx, cudaEventCreate(&e0), "queue timing");
+            if (st == EDM_OK) st = cuda_check(ctx, cudaEventCreate(&e1), "queue timing");
+            if (st == EDM_OK) st = cuda_check(ctx, cudaEventRecord(e0, stream), "queue timing");
+            if (st != EDM_OK) return st;
+        }
+        before_launch(ctx);
+        kern<<<grid, SX_WARPS * 32, smem, stream>>>(P.d_jobs + P.job0[k], P.njob[k], P.items[k],
+                                                    P.d_counters + k, E_max, Tp_sel,
+                                                    diag_stats(ctx));
+        st = after_launch(ctx, k == SQ_LONG ? "sweep_long_queue_kernel" : "sweep_queue_kernel");
+        if (ms) {
+            edm_status t = cuda_check(ctx, cudaEventRecord(e1, stream), "queue timing");
+            if (t == EDM_OK) t = cuda_check(ctx, cudaEventSynchronize(e1), "queue timing");
+            if (t == EDM_OK) t = cuda_check(ctx, cudaEventElapsedTime(&ms[k], e0, e1), "queue timing");
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (st == EDM_OK) st = t;
+        }
+        if (st != EDM_OK) return st;
+    }
+    before_launch(ctx);
+    simplex_finish_jobs_kernel<<<static_cast<unsigned>((P.series_total + 127) / 128), 128, 0,
+                                 stream>>>(P.d_jobs, P.d_series0, P.njobs, P.series_total, E_max,
+                                           Tp_sel);
+    return after_launch(ctx, "simplex_finish_kernel");
+}
+
+// Autotuner of the queues (before any capture: it times launches): for every
+// kind of this batch not tuned yet, run the batch with 128, 256 and 512
+// query times per work item and keep, per kind, the fastest.
+static edm_status tune_sweep_queue(edm_ctx *ctx, const edm_instance *inst, int n, int E_max,
+                                   int Tp_sel, int32_t *const *E_out) {
+    bool need = false;
+    for (int i = 0; i < n; ++i) {
+        const uint64_t key = 0x5157000000000000ull |
+                             static_cast<uint64_t>(sweep_kind(inst[i].L, E_max, inst[i].tau));
+        if (!ctx->tune->count(key)) need = true;
+    }
+    if (!need) return EDM_OK;
+    const int cands[3] = {128, 256, 512};
+    float best_ms[SQ_KINDS];
+    int best_rows[SQ_KINDS];
+    for (int k = 0; k < SQ_KINDS; ++k) {
+        best_ms[k] = 0.f;
+        best_rows[k] = 0;
+    }
+    for (int c : cands) {
+        int rows[SQ_KINDS];
+        for (int k = 0; k < SQ_KINDS; ++k) rows[k] = c;
+        SweepQueuePlan P;
+        edm_status st = plan_sweep_queue(ctx, inst, n, E_max, E_out, rows, P);
+        if (st != EDM_OK) return st;
+        float ms[SQ_KINDS] = {};
+        st = enqueue_sweep_queue(ctx, P, E_max, Tp_sel, ctx->stream, ms);
+        if (st != EDM_OK) return st;
+        for (int k : P.kinds)
+            if (best_rows[k] == 0 || ms[k] < best_ms[k]) {
+                best_ms[k] = ms[k];
+                best_rows[k] = c;
+            }
+    }
+    for (int k = 0; k < SQ_KINDS; ++k)
+        if (best_rows[k]) (*ctx->tune)[0x5157000000000000ull | static_cast<uint64_t>(k)] = best_rows[k];
+    return EDM_OK;
+}
+
+edm_status launch_simplex_queue(edm_ctx *ctx, const edm_instance *inst, int n, int E_max,
+                                int Tp_sel, int32_t *const *E_out, bool tune, bool capture) {
+    if (tune && ctx->autotune) {
+        edm_status st = tune_sweep_queue(ctx, inst, n, E_max, Tp_sel, E_out);
+        if (st != EDM_OK) return st;
+    }
+    int rows[SQ_KINDS];
+    for (int k = 0; k < SQ_KINDS; ++k) rows[k] = queue_rows(ctx, k);
+    SweepQueuePlan P;
+    edm_status st = plan_sweep_queue(ctx, inst, n, E_max, E_out, rows, P);
+    if (st != EDM_OK) return st;
+    if (!capture) return enqueue_sweep_queue(ctx, P, E_max, Tp_sel, ctx->stream, nullptr);
+    // one graph of the whole batch, replayed while the batch and the tuned
+    // values stay the same
+    uint64_t key = 1469598103934665603ull;
+    auto mix = [&](const void *p, size_t b) {
+        const unsigned char *c = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < b; ++i) key = (key ^ c[i]) * 1099511628211ull;
+    };
+    mix("sweepq", 6);
+    mix(&E_max, sizeof(E_max));
+    mix(&Tp_sel, sizeof(Tp_sel));
+    mix(rows, sizeof(rows));
+    for (int i = 0; i < n; ++i) {
+        mix(&inst[i], sizeof(inst[i]));
+        mix(&E_out[i], sizeof(E_out[i]));
+    }
+    mix(&P.d_jobs, sizeof(P.d_jobs));
+    if (!ctx->qgraph_exec || ctx->qgraph_key != key) {
+        if (ctx->qgraph_exec) cudaGraphExecDestroy(ctx->qgraph_exec);
+        ctx->qgraph_exec = nullptr;
+        if (!ctx->origin &&
+            cudaStreamCreateWithFlags(&ctx->origin, cudaStreamNonBlocking) != cudaSuccess)
+            return set_error(ctx, EDM_ERR_CUDA, "batch stream creation failed");
+        if (cudaStreamBeginCapture(ctx->origin, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+            return set_error(ctx, EDM_ERR_CUDA, "graph capture could not begin");
+        const uint64_t before = ctx->launches;
+        st = enqueue_sweep_queue(ctx, P, E_max, Tp_sel, ctx->origin, nullptr);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(ctx->origin, &graph);
+        if (st != EDM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (ce != cudaSuccess || !graph) return cuda_check(ctx, ce, "graph capture");
+        const cudaError_t ie = cudaGraphInstantiate(&ctx->qgraph_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return cuda_check(ctx, ie, "graph instantiation");
+        ctx->qgraph_key = key;
+        ctx->qgraph_kernels = ctx->launches - before;
+        ctx->launches = before;
+    }
+    if (!ctx->ev_fork)
+        st = cuda_check(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming),
+                        "batch event");
+    if (st == EDM_OK && !ctx->ev_done)
+        st = cuda_check(ctx, cudaEventCreateWithFlags(&ctx->ev_done, cudaEventDisableTiming),
+                        "batch event");
+    if (st == EDM_OK) st = cuda_check(ctx, cudaEventRecord(ctx->ev_fork, ctx->stream), "batch order");
+    if (st == EDM_OK)
+        st = cuda_check(ctx, cudaStreamWaitEvent(ctx->origin, ctx->ev_fork, 0), "batch order");
+    if (st == EDM_OK)
+        st = cuda_check(ctx, cudaGraphLaunch(ctx->qgraph_exec, ctx->origin), "graph launch");
+    if (st == EDM_OK) st = cuda_check(ctx, cudaEventRecord(ctx->ev_done, ctx->origin), "batch order");
+    if (st == EDM_OK)
+        st = cuda_check(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_done, 0), "batch order");
+    if (st != EDM_OK) return st;
+    ctx->launches += ctx->qgraph_kernels;
+    return EDM_OK;
 }
 
 // ---------------------------------------------------------------------------
