@@ -209,6 +209,11 @@ __device__ __forceinline__ bool table_slot(const CcmGroups &g, uint8_t *tables, 
     return true;
 }
 
+// Resident CTAs per SM that the register budget of the table builder is set
+// for: the distances take CH registers a thread, and with these bounds no
+// slot count spills.
+constexpr int table_min_blocks(int CH) { return CH <= 24 ? 3 : CH <= 48 ? 2 : 1; }
+
 // Register-resident variant for series of up to 32*CH points: the FP32
 // distances from x(t) to every candidate are accumulated lag by lag in
 // registers (lag order 0..E-1, the same operations as dist32) and the
@@ -216,7 +221,7 @@ __device__ __forceinline__ bool table_slot(const CcmGroups &g, uint8_t *tables, 
 // the candidates.  HEAD1: every lag offset (E-1)tau is below 32, so only
 // candidate slot 0 can reach before the start of the series.
 template <int CH, bool HEAD1>
-__global__ void __launch_bounds__(KNN_WARPS * 32)
+__global__ void __launch_bounds__(KNN_WARPS * 32, table_min_blocks(CH))
     ccm_table_regs_kernel(const float *__restrict__ X, long long ld, int L, int tau, int Tp,
                           int RB, const CcmGroups g, uint8_t *__restrict__ tables,
                           unsigned long long *stats) {

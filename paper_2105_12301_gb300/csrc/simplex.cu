@@ -50,20 +50,32 @@ __device__ __forceinline__ float simplex_predict(float d, int u, const float *xs
 // registers (select_set_regs) is shared with the neighbour-table builder.
 //
 // A warp owns one query time t and keeps the FP32 squared distance from x(t)
-// to every candidate u = lane + 32 j in registers.  Going from E-1 to E adds
-// one lag: s = fma(d, d, s) with d = X[t-(E-1)tau] - X[u-(E-1)tau], which is
-// exactly the operation sequence of the direct sum over l = 0..E-1, so the
-// values are bit-identical to those of knn_row.  Candidates below the first
-// point of P_E, past its last point, or equal to t hold +inf.  Each E then
-// selects from the registers: lane minimum, the (K+1)-th smallest of the 32
-// minima as a bound, ballot-compaction of every value at or below it into
-// the warp buffer, exact ranking of the few collected keys, and the FP64
-// band check of knn_row's KNN_SET mode.
+// to every candidate u = lane + 32 j in registers (slot j), so that
+// neighbouring times -- often neighbours of t together on a smooth series --
+// sit in different lanes and the lane minima below make a tight bound.
+// Going from E-1 to E adds one lag: s = fma(d, d, s) with d = X[t-(E-1)tau]
+// - X[u-(E-1)tau], which is exactly the operation sequence of the direct sum
+// over l = 0..E-1, so the values are bit-identical to those of knn_row.
+// Candidates below the first point of P_E, past its last point, or equal to
+// t hold +inf.  Each E then selects from the registers: lane minimum, the
+// (K+1)-th smallest of the 32 minima as a bound, compaction of every value at
+// or below it through 4-slot cells, exact ranking of the few collected keys,
+// and the FP64 band check of knn_row's KNN_SET mode.  The neighbour set of
+// every E is written to the warp's list; after the last E, lane E-1 forms the
+// simplex prediction of E from it (section 2.1 step 4) and accumulates its
+// moments, so the per-E work holds no warp-wide reduction.
+
+constexpr int SX_NB = 232;  // per-warp neighbour lists: sum over E = 1..20 of (E+1) = 230
+static_assert(EDM_E_MAX <= 20, "the neighbour lists hold E = 1..20");
+
+// First entry of the list of E (K = E+1 entries each).
+__device__ __forceinline__ int nb_off(int E) { return (E - 1) * (E + 2) / 2; }
 
 template <int CH, bool HEAD1>
 __device__ __forceinline__ void sweep_row(const float *xs, int t, int hi, int E_max, int tau,
-                                          int Tp, float mu, WarpScratch *ws, float (&m)[5],
-                                          unsigned keep, FallbackCount &fc) {
+                                          int Tp, float mu, WarpScratch *ws, float2 *nb,
+                                          float (&m)[5], unsigned keep, FallbackCount &fc) {
+    static_assert(CH % 4 == 0, "4-slot cells");
     const int lane = lane_id();
     float s[CH];
 #pragma unroll
@@ -71,6 +83,7 @@ __device__ __forceinline__ void sweep_row(const float *xs, int t, int hi, int E_
         const int u = lane + 32 * j;
         s[j] = (u <= hi && u != t) ? 0.f : EDM_INF;
     }
+    int E_row = 0;
     for (int E = 1; E <= E_max; ++E) {
         const int lo = (E - 1) * tau;
         if (t < lo || hi - lo + 1 < E + 2) break;
@@ -93,16 +106,47 @@ __device__ __forceinline__ void sweep_row(const float *xs, int t, int hi, int E_
         int u_out = 0;
         float d_out = 0.f;
         fc.add(select_set_regs<CH>(s, xs, t, lo, hi, E, tau, K, ws, u_out, d_out, keep));
-        const float a = simplex_predict(d_out, u_out, xs, Tp, mu, K);
-        const float b = __fsub_rn(xs[t + Tp], mu);
-        if (lane == E - 1) {
-            m[0] += a;
-            m[1] += b;
-            m[2] = __fmaf_rn(a, a, m[2]);
-            m[3] = __fmaf_rn(b, b, m[3]);
-            m[4] = __fmaf_rn(a, b, m[4]);
-        }
+        if (lane < K) nb[nb_off(E) + lane] = make_float2(d_out, __int_as_float(u_out));
+        E_row = E;
     }
+    __syncwarp();
+    // lane E-1: simplex prediction of x(t+Tp) from the K neighbours of E,
+    // sum_r w_r y_r / sum_r w_r with w_r = exp(-d_r/d_1) (or the d_1 = 0
+    // limit) and y_r = x[u_r+Tp] - mu, then the moments of (prediction,
+    // observation)
+    if (lane < E_row) {
+        const int K = lane + 2;
+        const float2 *list = nb + nb_off(lane + 1);
+        const float d1 = list[0].x;
+        float w_sum = 0.f, wy_sum = 0.f;
+        for (int r = 0; r < K; ++r) {
+            const float2 e = list[r];
+            float w;
+            if (d1 > 0.f)
+                w = expf(-(e.x / d1));
+            else
+                w = (e.x == 0.f) ? 1.f : 0.f;
+            w_sum += w;
+            wy_sum = __fmaf_rn(w, __fsub_rn(xs[__float_as_int(e.y) + Tp], mu), wy_sum);
+        }
+        const float a = wy_sum / w_sum;
+        const float b = __fsub_rn(xs[t + Tp], mu);
+        m[0] += a;
+        m[1] += b;
+        m[2] = __fmaf_rn(a, a, m[2]);
+        m[3] = __fmaf_rn(b, b, m[3]);
+        m[4] = __fmaf_rn(a, b, m[4]);
+    }
+    __syncwarp();
+}
+
+// Dynamic shared memory of sweep_block: per-warp scratch and neighbour
+// lists, the moment reduction buffer, the series mean partials, and the
+// series (32*CH points, zero past its end) behind 32 points of padding.
+inline size_t sweep_smem_bytes(int CH) {
+    return SX_WARPS * sizeof(WarpScratch) + SX_WARPS * 32 * 5 * sizeof(float) +
+           SX_WARPS * sizeof(double) + SX_WARPS * SX_NB * sizeof(float2) +
+           sizeof(float) * (32 + 32 * static_cast<size_t>(CH));
 }
 
 // One CTA-sized block of work: series `series` (staged in shared memory,
@@ -118,26 +162,29 @@ __device__ __forceinline__ void sweep_block(uint8_t *smem, const float *__restri
     WarpScratch *wsa = reinterpret_cast<WarpScratch *>(smem);
     float *red = reinterpret_cast<float *>(smem + SX_WARPS * sizeof(WarpScratch));
     double *mu_s = reinterpret_cast<double *>(red + SX_WARPS * 32 * 5);
-    float *xs = reinterpret_cast<float *>(mu_s + SX_WARPS);
+    float2 *nba = reinterpret_cast<float2 *>(mu_s + SX_WARPS);
+    float *xs = reinterpret_cast<float *>(nba + SX_WARPS * SX_NB) + 32;
     const int warp = threadIdx.x >> 5, lane = lane_id();
     const float *xg = X + static_cast<size_t>(series) * L;
     double acc = 0.0;
     for (int i = threadIdx.x; i < L; i += blockDim.x) acc += static_cast<double>(xg[i]);
     acc = warp_sum_d(acc);
     if (lane == 0) mu_s[warp] = acc;
-    for (int i = threadIdx.x; i < 32 * CH; i += blockDim.x) xs[i] = i < L ? xg[i] : 0.f;
+    for (int i = static_cast<int>(threadIdx.x) - 32; i < 32 * CH; i += blockDim.x)
+        xs[i] = (i >= 0 && i < L) ? xg[i] : 0.f;
     __syncthreads();
     double tot = 0.0;
     for (int w = 0; w < SX_WARPS; ++w) tot += mu_s[w];
     const float mu = static_cast<float>(tot / L);
     float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     WarpScratch *ws = wsa + warp;
+    float2 *nb = nba + warp * SX_NB;
     const int hi = L - 1 - Tp;
     const int t1 = min(hi + 1, (rb + 1) * TB);
     const unsigned keep = bitonic_keep_min_bits();
     FallbackCount fc;
     for (int t = rb * TB + warp; t < t1; t += SX_WARPS)
-        sweep_row<CH, HEAD1>(xs, t, hi, E_max, tau, Tp, mu, ws, m, keep, fc);
+        sweep_row<CH, HEAD1>(xs, t, hi, E_max, tau, Tp, mu, ws, nb, m, keep, fc);
     fc.flush(stats);
 #pragma unroll
     for (int j = 0; j < 5; ++j) red[(warp * 32 + lane) * 5 + j] = m[j];
@@ -151,9 +198,13 @@ __device__ __forceinline__ void sweep_block(uint8_t *smem, const float *__restri
     __syncthreads();
 }
 
+// Two CTAs per SM up to 48 slots (the register file allows 128 registers a
+// thread); the 64-slot sweep needs about 200 and runs one CTA per SM.
+constexpr int sweep_min_blocks(int CH) { return CH <= 48 ? 2 : 1; }
+
 // One CTA per (series, block of query times).
 template <int CH, bool HEAD1>
-__global__ void __launch_bounds__(SX_WARPS * 32)
+__global__ void __launch_bounds__(SX_WARPS * 32, sweep_min_blocks(CH))
     sweep_kernel(const float *__restrict__ X, int L, int E_max, int tau, int Tp, int TB, int nrb,
                  double *__restrict__ partial, unsigned long long *stats) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -432,7 +483,7 @@ __device__ __forceinline__ int job_of(const SweepJob *jobs, int njobs, long long
 }
 
 template <int CH, bool HEAD1>
-__global__ void __launch_bounds__(SX_WARPS * 32)
+__global__ void __launch_bounds__(SX_WARPS * 32, sweep_min_blocks(CH))
     sweep_queue_kernel(const SweepJob *__restrict__ jobs, int njobs, long long nitems,
                        unsigned long long *counter, int E_max, int Tp,
                        unsigned long long *stats) {
@@ -551,8 +602,6 @@ edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max,
     edm_status st = ws_reserve(ctx, simplex_workspace_bytes(ctx, N, L, E_max));
     if (st != EDM_OK) return st;
     double *partial = static_cast<double *>(ctx->ws);
-    const size_t fixed = SX_WARPS * sizeof(WarpScratch) + SX_WARPS * 32 * 5 * sizeof(float) +
-                         SX_WARPS * sizeof(double);
     dim3 grid(N, nrb);
     const int ch = (L + 31) / 32;
     if (ch <= 64) {
@@ -561,7 +610,7 @@ edm_status launch_simplex(edm_ctx *ctx, const float *X, int N, int L, int E_max,
         int CH = 64;
         for (int c : CHs)
             if (c >= ch) { CH = c; break; }
-        const size_t smem = fixed + sizeof(float) * 32 * CH;
+        const size_t smem = sweep_smem_bytes(CH);
         void (*kern)(const float *, int, int, int, int, int, int, double *, unsigned long long *) = nullptr;
         const bool head1 = (E_max - 1) * tau < 32;
         switch (CH) {
@@ -643,7 +692,7 @@ static QueueKernel queue_kernel(int kind) {
 static size_t queue_smem(int kind, int L_max) {
     const size_t red = SX_WARPS * 32 * 5 * sizeof(float) + SX_WARPS * sizeof(double);
     if (kind == SQ_LONG) return SX_WARPS * sizeof(LongScratch) + red + align_up(sizeof(float) * L_max, 16);
-    return SX_WARPS * sizeof(WarpScratch) + red + sizeof(float) * 32 * SQ_CH[kind / 2];
+    return sweep_smem_bytes(SQ_CH[kind / 2]);
 }
 
 // Rows per work item of a kind: the tuned value if any, else 256.
@@ -966,13 +1015,11 @@ extern "C" edm_status edm_simplex_optimal_E_noalloc(const float *X, int N, int L
     dim3 grid(N, nrb);
     const int ch = (L + 31) / 32;
     if (ch <= 64) {
-        const size_t fixed = SX_WARPS * sizeof(WarpScratch) + SX_WARPS * 32 * 5 * sizeof(float) +
-                             SX_WARPS * sizeof(double);
         const int CHs[] = {8, 16, 24, 32, 48, 64};
         int CH = 64;
         for (int c : CHs)
             if (c >= ch) { CH = c; break; }
-        const size_t smem = fixed + sizeof(float) * 32 * CH;
+        const size_t smem = sweep_smem_bytes(CH);
         const bool head1 = (E_max - 1) * tau < 32;
         void (*kern)(const float *, int, int, int, int, int, int, double *, unsigned long long *) = nullptr;
         switch (CH) {
