@@ -10,7 +10,7 @@ Per workload it reports:
     that are near-ties (the oracle's skills of the two choices within 1e-5);
   - max |rho_E gpu - rho_E oracle| of the simplex sweep;
   - max and 99th percentile of |rho gpu - rho oracle| of all-to-all CCM with
-    FP32 and with BF16 target storage (the oracle always takes the GPU's E*).
+    FP32, FP16 and BF16 target storage (the oracle always takes the GPU's E*).
 Like the tests, this script is test infrastructure: it is the only kind of
 code besides tests that calls the oracle.
 """
@@ -71,7 +71,7 @@ def ccm_report(Xg, X, E_gpu, rows, tau, Tp, targets=None):
     out = {}
     Y = X if targets is None else X[targets]
     ref = oracle.ccm_matrix(X, Y, E_gpu, tau, Tp, lib_rows=rows)
-    for prec in ("fp32", "bf16"):
+    for prec in ("fp32", "fp16", "bf16"):
         rho = edm.edm_ccm_all(Xg, Xg, gpu(E_gpu.astype(np.int32)), tau, Tp, prec)
         edm.edm_ctx_sync()
         got = rho[rows].cpu().numpy()
@@ -147,7 +147,7 @@ def main():
         w = {}
         Xw = np.ascontiguousarray(X[:, :L_lib])
         ref = oracle.ccm_matrix(Xw[lib_rows], Xw[tgts], E_np[lib_rows], 1, 0)
-        for prec in ("fp32", "bf16"):
+        for prec in ("fp32", "fp16", "bf16"):
             rho = edm.edm_ccm_window(Xg, 0, L_lib, E_full, 1, 0, prec)
             edm.edm_ctx_sync()
             got = rho.cpu().numpy()[np.ix_(lib_rows, tgts)]
