@@ -212,7 +212,7 @@ __device__ __forceinline__ bool table_slot(const CcmGroups &g, uint8_t *tables, 
 // Resident CTAs per SM that the register budget of the table builder is set
 // for: the distances take CH registers a thread, and with these bounds no
 // slot count spills.
-constexpr int table_min_blocks(int CH) { return CH <= 24 ? 3 : CH <= 48 ? 2 : 1; }
+constexpr int table_min_blocks(int CH) { return CH >= 16 && CH <= 24 ? 3 : CH <= 48 ? 2 : 1; }
 
 // Register-resident variant for series of up to 32*CH points: the FP32
 // distances from x(t) to every candidate are accumulated lag by lag in

@@ -382,13 +382,9 @@ __device__ __forceinline__ int compact_le(const float (&s)[CH], float bound, War
     for (int j = 0; j < CH; ++j) {
         const bool p = s[j] <= bound && s[j] != EDM_INF;
         const unsigned b = __ballot_sync(FULL, p);
-        if (b) {
-            if (p) {
-                const int pos = base + __popc(b & lt);
-                if (pos < KNN_CAP) ws->key[pos] = mk_key(s[j], u0 + slot_u<PAIR>(lane, j));
-            }
-            base += __popc(b);
-        }
+        const int pos = base + __popc(b & lt);
+        if (p && pos < KNN_CAP) ws->key[pos] = mk_key(s[j], u0 + slot_u<PAIR>(lane, j));
+        base += __popc(b);
     }
     __syncwarp();
     return base;
@@ -414,10 +410,8 @@ __device__ __forceinline__ int compact_le_groups(const float (&s)[CH], const flo
                 const int j = 4 * g + i;
                 const bool p = s[j] <= bound;
                 const unsigned b = __ballot_sync(FULL, p);
-                if (p) {
-                    const int pos = base + __popc(b & lt);
-                    if (pos < KNN_CAP) ws->key[pos] = mk_key(s[j], u0 + slot_u<PAIR>(lane, j));
-                }
+                const int pos = base + __popc(b & lt);
+                if (p && pos < KNN_CAP) ws->key[pos] = mk_key(s[j], u0 + slot_u<PAIR>(lane, j));
                 base += __popc(b);
             }
         }
@@ -428,35 +422,43 @@ __device__ __forceinline__ int compact_le_groups(const float (&s)[CH], const flo
 
 // Compact the 4-slot cells (lane, group g) whose minimum gm[g] is at or below
 // a FINITE bound into ws->cell_v / ws->cell_u: the lane writes the cell's four
-// values and the time index of its first slot, u0 + slot_u(lane, 4 g).  Visits
-// only the groups in which some lane holds such a cell.  Returns the number
-// of cells (only the first KNN_CELLS are stored).  On this data nearly every
-// value at or below the lane-minimum bound is the minimum of its cell, so a
-// cell is written with one 16-byte store where compact_le_groups spends a
-// ballot on each of its four slots.
+// values and the time index of its first slot, u0 + slot_u(lane, 4 g).
+// Returns the number of cells (only the first KNN_CELLS are stored).  On this
+// data nearly every value at or below the lane-minimum bound is the minimum
+// of its cell, so a cell is written with one 16-byte store where a ballot per
+// slot would be needed otherwise.  The code has no data-dependent branch:
+// each lane marks its cells in a bit mask, an inclusive warp scan of the mask
+// counts gives each lane its first position, and the stores are predicated.
+// (A ballot per group with a branch over the active groups costs far more
+// when the neighbours are scattered over many groups, as on chaotic series.)
 template <int CH, bool PAIR = false>
 __device__ __forceinline__ int compact_cells(const float (&s)[CH], const float (&gm)[CH / 4],
                                              float bound, WarpScratch *ws, int u0 = 0) {
+    constexpr int NG = CH / 4;
     const int lane = lane_id();
-    const unsigned lt = (1u << lane) - 1u;
-    int base = 0;
+    unsigned mask = 0;
 #pragma unroll
-    for (int g = 0; g < CH / 4; ++g) {
-        const bool p = gm[g] <= bound;
-        const unsigned b = __ballot_sync(FULL, p);
-        if (b) {
-            if (p) {
-                const int pos = base + __popc(b & lt);
-                if (pos < KNN_CELLS) {
-                    ws->cell_v[pos] = make_float4(s[4 * g], s[4 * g + 1], s[4 * g + 2], s[4 * g + 3]);
-                    ws->cell_u[pos] = u0 + slot_u<PAIR>(lane, 4 * g);
-                }
-            }
-            base += __popc(b);
+    for (int g = 0; g < NG; ++g) mask |= (gm[g] <= bound ? 1u : 0u) << g;
+    const int cnt = __popc(mask);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < WARP; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, incl, o);
+        incl += lane >= o ? v : 0;
+    }
+    const int M = __shfl_sync(FULL, incl, WARP - 1);
+    int pos = incl - cnt;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        const bool p = (mask >> g) & 1u;
+        if (p && pos < KNN_CELLS) {
+            ws->cell_v[pos] = make_float4(s[4 * g], s[4 * g + 1], s[4 * g + 2], s[4 * g + 3]);
+            ws->cell_u[pos] = u0 + slot_u<PAIR>(lane, 4 * g);
         }
+        pos += p ? 1 : 0;
     }
     __syncwarp();
-    return base;
+    return M;
 }
 
 // The keys of the values at or below `bound` in the first M (<= KNN_CELLS)
@@ -480,10 +482,8 @@ __device__ __forceinline__ int cells_to_keys(WarpScratch *ws, int M, float bound
         for (int i = 0; i < 4; ++i) {
             const bool p = vv[i] <= bound;
             const unsigned b = __ballot_sync(FULL, p);
-            if (p) {
-                const int pos = base + __popc(b & lt);
-                if (pos < KNN_CAP) ws->key[pos] = mk_key(vv[i], u0 + cell_off<PAIR>(i));
-            }
+            const int pos = base + __popc(b & lt);
+            if (p && pos < KNN_CAP) ws->key[pos] = mk_key(vv[i], u0 + cell_off<PAIR>(i));
             base += __popc(b);
         }
     }

@@ -21,30 +21,6 @@ namespace edm {
 constexpr int SX_WARPS = 8;
 constexpr int SX_SERIES_SMEM_MAX = 96 * 1024;
 
-// Simplex prediction from the K neighbours held one per lane (lane r < K
-// holds the r-th nearest: time u, distance d): sum_r w_r y_r / sum_r w_r with
-// w_r = exp(-d_r/d_1) (or the d_1 = 0 limit) and y_r = x[u_r+Tp] - mu.  The
-// two sums are reduced side by side.
-__device__ __forceinline__ float simplex_predict(float d, int u, const float *xs, int Tp, float mu,
-                                                 int K) {
-    const int lane = lane_id();
-    const float d1 = __shfl_sync(FULL, d, 0);
-    float w = 0.f, wy = 0.f;
-    if (lane < K) {
-        if (d1 > 0.f)
-            w = expf(-(d / d1));
-        else
-            w = (d == 0.f) ? 1.f : 0.f;
-        wy = w * __fsub_rn(xs[u + Tp], mu);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        w += __shfl_xor_sync(FULL, w, o);
-        wy += __shfl_xor_sync(FULL, wy, o);
-    }
-    return wy / w;
-}
-
 // ---------------------------------------------------------------------------
 // Incremental sweep over E (series of up to 32*CH points).  The selection from
 // registers (select_set_regs) is shared with the neighbour-table builder.
@@ -224,6 +200,8 @@ __global__ void __launch_bounds__(SX_WARPS * 32, sweep_min_blocks(CH))
 // chunk); those are compacted, merged with the list and ranked.  After the
 // last chunk every E has its exact FP32 top-R, and the band check of
 // knn_row's KNN_SET mode decides whether the FP64 ranking must be consulted.
+// Each E's list then takes its K neighbours, and lane E-1 forms the
+// prediction of E from them, as in sweep_row.
 
 constexpr int LS_CH = 32;          // candidate slots per lane per chunk
 constexpr int LS_LIST = 256;       // sum over E = 1..20 of (E+2) = 250 keys
@@ -388,16 +366,38 @@ __device__ void sweep_long_row(const float *xs, int L, int t, int hi, int E_max,
             }
         }
         __syncwarp();
-        const float a = simplex_predict(d_out, u_out, xs, Tp, mu, K);
-        const float b = __fsub_rn(xs[t + Tp], mu);
-        if (lane == E - 1) {
-            m[0] += a;
-            m[1] += b;
-            m[2] = __fmaf_rn(a, a, m[2]);
-            m[3] = __fmaf_rn(b, b, m[3]);
-            m[4] = __fmaf_rn(a, b, m[4]);
-        }
+        // the list of E is no longer needed: it now holds E's neighbours
+        if (lane < K)
+            reinterpret_cast<float2 *>(sc->list + ls_list_off(E))[lane] =
+                make_float2(d_out, __int_as_float(u_out));
+        __syncwarp();
     }
+    // lane E-1: simplex prediction of x(t+Tp) from the K neighbours of E and
+    // the moments of (prediction, observation), as in sweep_row
+    if (lane < E_row) {
+        const int K = lane + 2;
+        const float2 *nb = reinterpret_cast<const float2 *>(sc->list + ls_list_off(lane + 1));
+        const float d1 = nb[0].x;
+        float w_sum = 0.f, wy_sum = 0.f;
+        for (int r = 0; r < K; ++r) {
+            const float2 e = nb[r];
+            float w;
+            if (d1 > 0.f)
+                w = expf(-(e.x / d1));
+            else
+                w = (e.x == 0.f) ? 1.f : 0.f;
+            w_sum += w;
+            wy_sum = __fmaf_rn(w, __fsub_rn(xs[__float_as_int(e.y) + Tp], mu), wy_sum);
+        }
+        const float a = wy_sum / w_sum;
+        const float b = __fsub_rn(xs[t + Tp], mu);
+        m[0] += a;
+        m[1] += b;
+        m[2] = __fmaf_rn(a, a, m[2]);
+        m[3] = __fmaf_rn(b, b, m[3]);
+        m[4] = __fmaf_rn(a, b, m[4]);
+    }
+    __syncwarp();
 }
 
 template <bool SMEM>
@@ -444,7 +444,7 @@ __device__ __forceinline__ void sweep_long_block(uint8_t *smem, const float *__r
 }
 
 template <bool SMEM>
-__global__ void __launch_bounds__(SX_WARPS * 32)
+__global__ void __launch_bounds__(SX_WARPS * 32, 2)
     sweep_long_kernel(const float *__restrict__ X, int L, int E_max, int tau, int Tp, int TB,
                       int nrb, double *__restrict__ partial, unsigned long long *stats) {
     extern __shared__ __align__(16) uint8_t smem[];
@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(SX_WARPS * 32, sweep_min_blocks(CH))
     }
 }
 
-__global__ void __launch_bounds__(SX_WARPS * 32)
+__global__ void __launch_bounds__(SX_WARPS * 32, 2)
     sweep_long_queue_kernel(const SweepJob *__restrict__ jobs, int njobs, long long nitems,
                             unsigned long long *counter, int E_max, int Tp,
                             unsigned long long *stats) {
