@@ -132,14 +132,17 @@ __device__ __forceinline__ void rank_keys(WarpScratch *ws, int c, int R) {
     if (lane < c4 - c) ws->key[c + lane] = ~0ull;
     __syncwarp();
     const ulonglong2 *k2 = reinterpret_cast<const ulonglong2 *>(ws->key);
-    for (int e = lane; e < c; e += WARP) {
-        const uint64_t ke = ws->key[e];
+    // every lane runs every pass (no divergent loop); a lane past the last
+    // key ranks a copy of key c4-1 and stores nothing
+    for (int e0 = 0; e0 < c; e0 += WARP) {
+        const int e = e0 + lane;
+        const uint64_t ke = ws->key[min(e, c4 - 1)];
         int rank = 0;
         for (int e2 = 0; e2 < c4 / 2; e2 += 2) {
             const ulonglong2 a = k2[e2], b = k2[e2 + 1];
             rank += (a.x < ke) + (a.y < ke) + (b.x < ke) + (b.y < ke);
         }
-        if (rank < R) ws->sel[rank] = ke;
+        if (e < c && rank < R) ws->sel[rank] = ke;
     }
     __syncwarp();
 }
@@ -582,11 +585,10 @@ __device__ __forceinline__ int select_set_regs(const float (&s)[CH], const float
         rank_keys(ws, c, R);
         const float edge = band_edge(key_s(ws->sel[K - 1]), E);
         if (R <= K || key_s(ws->sel[K]) > edge) {
-            if (lane < K) {
-                const uint64_t k = ws->sel[lane];
-                u_out = key_u(k);
-                d_out = sqrtf(key_s(k));
-            }
+            // all lanes (no divergence); lanes >= K repeat entry K-1
+            const uint64_t k = ws->sel[min(lane, K - 1)];
+            u_out = key_u(k);
+            d_out = sqrtf(key_s(k));
             __syncwarp();
             return 0;
         }
