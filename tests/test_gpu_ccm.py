@@ -235,6 +235,34 @@ def test_register_path_boundaries(L, tau):
     check_ccm(X, X, E_lib, tau, 0, "fp32", TOL_FP32, lib_rows=[0, 4])
 
 
+@pytest.mark.parametrize("L", [600, 1500, 3000])
+def test_selection_through_long_runs_of_ties(L):
+    # libraries on a coarse value grid (3 to 8 levels): long runs of exactly
+    # tied squared distances drive the selection from registers (optimal-E
+    # sweep, table builder; the chunked variants at 3,000 points) through its
+    # rare paths: more collected values than the key buffer holds, the
+    # bisection of the bound, the FP64 band and the full FP64 scan.  Series 3
+    # is constant, so every distance ties and every skill is NaN (E* = 1); as
+    # a library it still runs through the table builder, but its row of rho
+    # is not compared: its nearly constant predictions make rho
+    # ill-conditioned in FP32 moments.
+    X = inputs.coupled_logistic(4, L, 900 + L)
+    Xq = (np.round(X * 2.0) / 2.0).astype(np.float32)
+    Xq[3] = 0.0
+    edm.edm_set_option("diagnostics", 1)
+    try:
+        edm.edm_fallback_counts()
+        E = check_optimal_E(Xq, 8)
+        band, brute = edm.edm_fallback_counts()
+        assert band > 0 and brute > 0, (band, brute)
+        assert E[3] == 1
+        check_ccm(Xq, X, E.astype(np.int32), 1, 0, "fp32", TOL_FP32, lib_rows=[0, 1, 2])
+        band, brute = edm.edm_fallback_counts()
+        assert band > 0 and brute > 0, (band, brute)
+    finally:
+        edm.edm_set_option("diagnostics", 0)
+
+
 @pytest.mark.parametrize("L,tau,Tp_sel", [(3100, 1, 1), (2600, 2, 1), (4000, 1, 2)])
 def test_optimal_E_long_series(L, tau, Tp_sel):
     # more than 2,048 points: the chunked incremental sweep
