@@ -320,22 +320,9 @@ __device__ int knn_row(const float *xs, int t, int lo, int hi, int tau, int K, W
 // ------------------------------------------ selection from register arrays
 //
 // A warp holds the FP32 squared distances of a query row in a register array
-// s[CH] per lane, in one of two layouts of the candidates u (u0 + ...):
-//   strided (PAIR = false): slot j of lane l is u0 + l + 32 j;
-//   paired  (PAIR = true):  slot j of lane l is u0 + 64 (j/2) + 2 l + j%2, so
-//     slots 2q and 2q+1 hold neighbouring candidates and one 8-byte shared
-//     load gives both their lagged values.
-// A 4-slot group g of lane l is a "cell": its first candidate is
-// cell_base(l, g) and value i of it is that plus cell_off(i).
-
-template <bool PAIR>
-__device__ __forceinline__ int slot_u(int lane, int j) {
-    return PAIR ? 64 * (j >> 1) + 2 * lane + (j & 1) : lane + 32 * j;
-}
-template <bool PAIR>
-__device__ __forceinline__ int cell_off(int i) {
-    return PAIR ? (i & 1) + 64 * (i >> 1) : 32 * i;
-}
+// s[CH] per lane: slot j of lane l is the candidate u0 + l + 32 j.  A 4-slot
+// group g of lane l is a "cell": its first candidate is u0 + l + 128 g and
+// value i of it is that plus 32 i.
 
 #define EDM_INF __int_as_float(0x7f800000)
 
@@ -375,7 +362,7 @@ __device__ __forceinline__ float warp_sorted_at_f(float v, int r) {
 // Compact the keys (s[j], u0+lane+32j) with s[j] <= bound (and finite, i.e. a
 // candidate of P_E) into ws->key; returns
 // how many there are (only the first KNN_CAP are stored).
-template <int CH, bool PAIR = false>
+template <int CH>
 __device__ __forceinline__ int compact_le(const float (&s)[CH], float bound, WarpScratch *ws,
                                           int u0 = 0) {
     const int lane = lane_id();
@@ -386,7 +373,7 @@ __device__ __forceinline__ int compact_le(const float (&s)[CH], float bound, War
         const bool p = s[j] <= bound && s[j] != EDM_INF;
         const unsigned b = __ballot_sync(FULL, p);
         const int pos = base + __popc(b & lt);
-        if (p && pos < KNN_CAP) ws->key[pos] = mk_key(s[j], u0 + slot_u<PAIR>(lane, j));
+        if (p && pos < KNN_CAP) ws->key[pos] = mk_key(s[j], u0 + lane + 32 * j);
         base += __popc(b);
     }
     __syncwarp();
@@ -399,7 +386,7 @@ __device__ __forceinline__ int compact_le(const float (&s)[CH], float bound, War
 // in which some lane holds such a value; returns how many there are (only
 // the first KNN_CAP are stored).  Finite bounds exclude the +inf
 // non-candidates by themselves.
-template <int CH, bool PAIR = false>
+template <int CH>
 __device__ __forceinline__ int compact_le_groups(const float (&s)[CH], const float (&gm)[CH / 4],
                                                  float bound, WarpScratch *ws, int u0 = 0) {
     const int lane = lane_id();
@@ -414,7 +401,7 @@ __device__ __forceinline__ int compact_le_groups(const float (&s)[CH], const flo
                 const bool p = s[j] <= bound;
                 const unsigned b = __ballot_sync(FULL, p);
                 const int pos = base + __popc(b & lt);
-                if (p && pos < KNN_CAP) ws->key[pos] = mk_key(s[j], u0 + slot_u<PAIR>(lane, j));
+                if (p && pos < KNN_CAP) ws->key[pos] = mk_key(s[j], u0 + lane + 32 * j);
                 base += __popc(b);
             }
         }
@@ -425,7 +412,7 @@ __device__ __forceinline__ int compact_le_groups(const float (&s)[CH], const flo
 
 // Compact the 4-slot cells (lane, group g) whose minimum gm[g] is at or below
 // a FINITE bound into ws->cell_v / ws->cell_u: the lane writes the cell's four
-// values and the time index of its first slot, u0 + slot_u(lane, 4 g).
+// values and the time index of its first slot, u0 + lane + 128 g.
 // Returns the number of cells (only the first KNN_CELLS are stored).  On this
 // data nearly every value at or below the lane-minimum bound is the minimum
 // of its cell, so a cell is written with one 16-byte store where a ballot per
@@ -434,7 +421,7 @@ __device__ __forceinline__ int compact_le_groups(const float (&s)[CH], const flo
 // counts gives each lane its first position, and the stores are predicated.
 // (A ballot per group with a branch over the active groups costs far more
 // when the neighbours are scattered over many groups, as on chaotic series.)
-template <int CH, bool PAIR = false>
+template <int CH>
 __device__ __forceinline__ int compact_cells(const float (&s)[CH], const float (&gm)[CH / 4],
                                              float bound, WarpScratch *ws, int u0 = 0) {
     constexpr int NG = CH / 4;
@@ -456,7 +443,7 @@ __device__ __forceinline__ int compact_cells(const float (&s)[CH], const float (
         const bool p = (mask >> g) & 1u;
         if (p && pos < KNN_CELLS) {
             ws->cell_v[pos] = make_float4(s[4 * g], s[4 * g + 1], s[4 * g + 2], s[4 * g + 3]);
-            ws->cell_u[pos] = u0 + slot_u<PAIR>(lane, 4 * g);
+            ws->cell_u[pos] = u0 + lane + 128 * g;
         }
         pos += p ? 1 : 0;
     }
@@ -466,8 +453,8 @@ __device__ __forceinline__ int compact_cells(const float (&s)[CH], const float (
 
 // The keys of the values at or below `bound` in the first M (<= KNN_CELLS)
 // cells, into ws->key; returns how many there are (at most 4 M; only the
-// first KNN_CAP are stored).  Value i of a cell is time u0 + cell_off(i).
-template <bool PAIR = false>
+// first KNN_CAP are stored).  Value i of a cell is the candidate 32 i past
+// the cell's first one (ws->cell_u).
 __device__ __forceinline__ int cells_to_keys(WarpScratch *ws, int M, float bound) {
     const int lane = lane_id();
     const unsigned lt = (1u << lane) - 1u;
@@ -486,7 +473,7 @@ __device__ __forceinline__ int cells_to_keys(WarpScratch *ws, int M, float bound
             const bool p = vv[i] <= bound;
             const unsigned b = __ballot_sync(FULL, p);
             const int pos = base + __popc(b & lt);
-            if (p && pos < KNN_CAP) ws->key[pos] = mk_key(vv[i], u0 + cell_off<PAIR>(i));
+            if (p && pos < KNN_CAP) ws->key[pos] = mk_key(vv[i], u0 + 32 * i);
             base += __popc(b);
         }
     }
@@ -543,14 +530,15 @@ __device__ __forceinline__ float shrink_bound(const float (&s)[CH], float hi, in
 
 // The K nearest candidates (exact FP64 neighbour set) of the query time t
 // from the FP32 squared distances held in registers: s[j] is the distance to
-// the candidate u = slot_u(lane, j), +inf when u is not a candidate.  Steps as in
+// the candidate u = lane + 32 j, +inf when u is not a candidate.  Steps as in
 // knn_row's KNN_SET mode: lane minima, the (K+1)-th smallest of them as a
 // bound, compaction of the values at or below it (through 4-slot cells),
 // exact ranking of the collected keys, then the band check (resolved in FP64
 // when it fails).  On return lane r < K holds the r-th neighbour and its
-// distance.  keep: bitonic_keep_min_bits() of this lane.  Returns KNN_USED_*
-// flags (the same in every lane).
-template <int CH, bool PAIR = false>
+// distance (other lanes hold values the caller must ignore).  keep:
+// bitonic_keep_min_bits() of this lane.  Returns KNN_USED_* flags (the same
+// in every lane).
+template <int CH>
 __device__ __forceinline__ int select_set_regs(const float (&s)[CH], const float *xs, int t,
                                                int lo, int hi, int E, int tau, int K,
                                                WarpScratch *ws, int &u_out, float &d_out,
@@ -569,16 +557,16 @@ __device__ __forceinline__ int select_set_regs(const float (&s)[CH], const float
     // a finite theta excludes the +inf non-candidates by itself
     int c;
     if (theta == EDM_INF) {
-        c = compact_le<CH, PAIR>(s, theta, ws);
+        c = compact_le<CH>(s, theta, ws);
     } else {
-        const int M = compact_cells<CH, PAIR>(s, gm, theta, ws);
-        c = M <= KNN_CELLS ? cells_to_keys<PAIR>(ws, M, theta)
-                           : compact_le_groups<CH, PAIR>(s, gm, theta, ws);
+        const int M = compact_cells<CH>(s, gm, theta, ws);
+        c = M <= KNN_CELLS ? cells_to_keys(ws, M, theta)
+                           : compact_le_groups<CH>(s, gm, theta, ws);
     }
     if (c > KNN_CAP) {
         // a loose threshold: shrink it so that the values under it fit
         const float b = shrink_bound<CH>(s, theta, c, R, KNN_CAP, [](float) { return 0; });
-        if (b >= 0.f) c = compact_le_groups<CH, PAIR>(s, gm, b, ws);
+        if (b >= 0.f) c = compact_le_groups<CH>(s, gm, b, ws);
     }
     int flags = 0;
     if (c <= KNN_CAP) {
@@ -594,7 +582,7 @@ __device__ __forceinline__ int select_set_regs(const float (&s)[CH], const float
         }
         // resolve the band in FP64
         flags = KNN_USED_BAND;
-        c = compact_le<CH, PAIR>(s, edge, ws);
+        c = compact_le<CH>(s, edge, ws);
         if (c <= KNN_CAP) {
             rank_band_fp64(xs, t, E, tau, ws, c, K);
         } else {
