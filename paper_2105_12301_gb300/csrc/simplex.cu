@@ -47,6 +47,34 @@ static_assert(EDM_E_MAX <= 20, "the neighbour lists hold E = 1..20");
 // First entry of the list of E (K = E+1 entries each).
 __device__ __forceinline__ int nb_off(int E) { return (E - 1) * (E + 2) / 2; }
 
+// Simplex prediction of x(t+Tp) from the K neighbours of one E held in a
+// list (distance d_r, time u_r as float bits; entry 0 the nearest):
+// sum_r w_r y_r / sum_r w_r with w_r = exp(-d_r/d_1) (or the d_1 = 0 limit)
+// and y_r = x[u_r+Tp] - mu (section 2.1 steps 3-4), accumulated with the
+// observation into the moments m (sums of a, b, a^2, b^2, ab).
+__device__ __forceinline__ void predict_into_moments(const float2 *nb, int K, const float *xs,
+                                                     int t, int Tp, float mu, float (&m)[5]) {
+    const float d1 = nb[0].x;
+    float w_sum = 0.f, wy_sum = 0.f;
+    for (int r = 0; r < K; ++r) {
+        const float2 e = nb[r];
+        float w;
+        if (d1 > 0.f)
+            w = expf(-(e.x / d1));
+        else
+            w = (e.x == 0.f) ? 1.f : 0.f;
+        w_sum += w;
+        wy_sum = __fmaf_rn(w, __fsub_rn(xs[__float_as_int(e.y) + Tp], mu), wy_sum);
+    }
+    const float a = wy_sum / w_sum;
+    const float b = __fsub_rn(xs[t + Tp], mu);
+    m[0] += a;
+    m[1] += b;
+    m[2] = __fmaf_rn(a, a, m[2]);
+    m[3] = __fmaf_rn(b, b, m[3]);
+    m[4] = __fmaf_rn(a, b, m[4]);
+}
+
 template <int CH, bool HEAD1>
 __device__ __forceinline__ void sweep_row(const float *xs, int t, int hi, int E_max, int tau,
                                           int Tp, float mu, WarpScratch *ws, float2 *nb,
@@ -86,33 +114,8 @@ __device__ __forceinline__ void sweep_row(const float *xs, int t, int hi, int E_
         E_row = E;
     }
     __syncwarp();
-    // lane E-1: simplex prediction of x(t+Tp) from the K neighbours of E,
-    // sum_r w_r y_r / sum_r w_r with w_r = exp(-d_r/d_1) (or the d_1 = 0
-    // limit) and y_r = x[u_r+Tp] - mu, then the moments of (prediction,
-    // observation)
-    if (lane < E_row) {
-        const int K = lane + 2;
-        const float2 *list = nb + nb_off(lane + 1);
-        const float d1 = list[0].x;
-        float w_sum = 0.f, wy_sum = 0.f;
-        for (int r = 0; r < K; ++r) {
-            const float2 e = list[r];
-            float w;
-            if (d1 > 0.f)
-                w = expf(-(e.x / d1));
-            else
-                w = (e.x == 0.f) ? 1.f : 0.f;
-            w_sum += w;
-            wy_sum = __fmaf_rn(w, __fsub_rn(xs[__float_as_int(e.y) + Tp], mu), wy_sum);
-        }
-        const float a = wy_sum / w_sum;
-        const float b = __fsub_rn(xs[t + Tp], mu);
-        m[0] += a;
-        m[1] += b;
-        m[2] = __fmaf_rn(a, a, m[2]);
-        m[3] = __fmaf_rn(b, b, m[3]);
-        m[4] = __fmaf_rn(a, b, m[4]);
-    }
+    // lane E-1: prediction and moments of E
+    if (lane < E_row) predict_into_moments(nb + nb_off(lane + 1), lane + 2, xs, t, Tp, mu, m);
     __syncwarp();
 }
 
@@ -175,7 +178,7 @@ __device__ __forceinline__ void sweep_block(uint8_t *smem, const float *__restri
 }
 
 // Two CTAs per SM up to 48 slots (the register file allows 128 registers a
-// thread); the 64-slot sweep needs about 200 and runs one CTA per SM.
+// thread); the 64-slot sweep needs more than 200 and runs one CTA per SM.
 constexpr int sweep_min_blocks(int CH) { return CH <= 48 ? 2 : 1; }
 
 // One CTA per (series, block of query times).
@@ -372,31 +375,10 @@ __device__ void sweep_long_row(const float *xs, int L, int t, int hi, int E_max,
                 make_float2(d_out, __int_as_float(u_out));
         __syncwarp();
     }
-    // lane E-1: simplex prediction of x(t+Tp) from the K neighbours of E and
-    // the moments of (prediction, observation), as in sweep_row
-    if (lane < E_row) {
-        const int K = lane + 2;
-        const float2 *nb = reinterpret_cast<const float2 *>(sc->list + ls_list_off(lane + 1));
-        const float d1 = nb[0].x;
-        float w_sum = 0.f, wy_sum = 0.f;
-        for (int r = 0; r < K; ++r) {
-            const float2 e = nb[r];
-            float w;
-            if (d1 > 0.f)
-                w = expf(-(e.x / d1));
-            else
-                w = (e.x == 0.f) ? 1.f : 0.f;
-            w_sum += w;
-            wy_sum = __fmaf_rn(w, __fsub_rn(xs[__float_as_int(e.y) + Tp], mu), wy_sum);
-        }
-        const float a = wy_sum / w_sum;
-        const float b = __fsub_rn(xs[t + Tp], mu);
-        m[0] += a;
-        m[1] += b;
-        m[2] = __fmaf_rn(a, a, m[2]);
-        m[3] = __fmaf_rn(b, b, m[3]);
-        m[4] = __fmaf_rn(a, b, m[4]);
-    }
+    // lane E-1: prediction and moments of E, as in sweep_row
+    if (lane < E_row)
+        predict_into_moments(reinterpret_cast<const float2 *>(sc->list + ls_list_off(lane + 1)),
+                             lane + 2, xs, t, Tp, mu, m);
     __syncwarp();
 }
 
